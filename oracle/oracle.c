@@ -1,0 +1,404 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU lattice Boltzmann reference.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the graft smoke check and the benchmark's
+ * CPU-baseline arm do.  It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (paper Sec. 2, Eqs. 1-6, and Sec. 3.1 for the lists):
+ *   - the macroscopic moments rho = sum f_i, rho*u = sum c_i f_i        (Eq. 1)
+ *   - collide  f~_i = f_i + Omega_i                                      (Eq. 3)
+ *     with SRT  Omega_i = -omega (f_i - f_i^eq)                           (Eq. 5)
+ *     or TRT (two relaxation rates on the even/odd parts; textbook form,
+ *     the paper names TRT in Sec. 4 and cites the LBM textbook for it),
+ *     second-order equilibrium f_i^eq                                     (Eq. 6)
+ *     and a Guo body-force source (the paper says only "a force model",
+ *     Sec. 4; the Guo form is our reading)
+ *   - stream   f_i(x + c_i, t+1) = f~_i(x, t)                             (Eq. 4)
+ *     as a two-grid PUSH over a dense, direct-addressed box (Sec. 3),
+ *     with halfway bounce-back at walls (Sec. 3.1.1), periodic wrap,
+ *     a Ladd moving-wall (UBB) inlet and a linearised anti-bounce-back
+ *     pressure outlet (both textbook forms; the paper only says such
+ *     boundaries exist, Sec. 3.1.1).
+ *   - its own sparse indexing (Sec. 3.1): the compacted fluid-cell order
+ *     (lexicographic, x fastest), the pull index-list P(i,k) with no-slip
+ *     links pointing at the same cell's inverse direction and periodic links
+ *     wrapped, and a sparse two-grid pull stepper that uses the same per-cell
+ *     arithmetic as the dense stepper.
+ *
+ * PDFs are stored unshifted (f, not f - w) in FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ORC_FLUID = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3 };
+enum { ORC_SRT = 0, ORC_TRT = 1 };
+
+/* Velocity set, directions written out one by one (D3Q19 is the first 19
+ * rows of D3Q27).  Ordering convention: rest, then the six axis directions,
+ * then the twelve edge directions, then the eight corners, each followed
+ * immediately by its inverse. */
+static const int VEL[27][3] = {
+    {0, 0, 0},
+    {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1},
+    {1, 0, -1},  {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},
+    {1, 1, 1},   {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1},
+    {-1, 1, 1},  {1, -1, -1}};
+
+typedef struct {
+    int32_t nx, ny, nz;
+    const uint8_t *flags;      /* nx*ny*nz, x fastest */
+    uint32_t periodic;         /* bit0 x, bit1 y, bit2 z */
+    int32_t q;                 /* 19 or 27 */
+    int32_t op;                /* ORC_SRT or ORC_TRT */
+    double omega_plus;         /* 1/tau */
+    double omega_minus;        /* TRT odd rate (ignored for SRT) */
+    double force[3];           /* body-force density (Guo) */
+    const double *inlet_u;     /* 3 per inlet voxel, ascending voxel order; may be NULL */
+    double rho_out;            /* outlet density */
+} orc_problem;
+
+/* ---------------------------------------------------------------- stencil */
+
+/* Weight of a direction from its squared length (D3Q19 / D3Q27 textbook
+ * values). */
+static double weight(int q, int i) {
+    int n2 = VEL[i][0] * VEL[i][0] + VEL[i][1] * VEL[i][1] + VEL[i][2] * VEL[i][2];
+    if (q == 19) {
+        if (n2 == 0) return 1.0 / 3.0;
+        if (n2 == 1) return 1.0 / 18.0;
+        return 1.0 / 36.0;
+    }
+    if (n2 == 0) return 8.0 / 27.0;
+    if (n2 == 1) return 2.0 / 27.0;
+    if (n2 == 2) return 1.0 / 54.0;
+    return 1.0 / 216.0;
+}
+
+/* Inverse direction, found by searching the table for -c_i. */
+static int inverse(int q, int i) {
+    for (int j = 0; j < q; ++j)
+        if (VEL[j][0] == -VEL[i][0] && VEL[j][1] == -VEL[i][1] && VEL[j][2] == -VEL[i][2])
+            return j;
+    return -1;
+}
+
+int orc_stencil(int q, int32_t *c, double *w, int32_t *inv) {
+    if (q != 19 && q != 27) return -1;
+    for (int i = 0; i < q; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = VEL[i][a];
+        w[i] = weight(q, i);
+        inv[i] = inverse(q, i);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------- per-cell arithmetic */
+
+/* Eq. 6, c_s^2 = 1/3. */
+void orc_equilibrium(int q, double rho, const double u[3], double *feq) {
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < q; ++i) {
+        double cu = VEL[i][0] * u[0] + VEL[i][1] * u[1] + VEL[i][2] * u[2];
+        feq[i] = weight(q, i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+/* Guo source S_i = w_i [ 3 (c_i - u) + 9 (c_i . u) c_i ] . F  (without the
+ * (1 - omega/2) prefactor, which the collision applies). */
+void orc_guo_source(int q, const double u[3], const double F[3], double *S) {
+    double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    for (int i = 0; i < q; ++i) {
+        double cu = VEL[i][0] * u[0] + VEL[i][1] * u[1] + VEL[i][2] * u[2];
+        double cF = VEL[i][0] * F[0] + VEL[i][1] * F[1] + VEL[i][2] * F[2];
+        S[i] = weight(q, i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+    }
+}
+
+/* Eq. 1 with the Guo half-force velocity: rho = sum f, u = (sum c f + F/2)/rho. */
+void orc_moments(int q, const double *f, const double F[3], double *rho_out, double u_out[3]) {
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < q; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) j[a] += VEL[i][a] * f[i];
+    }
+    *rho_out = rho;
+    for (int a = 0; a < 3; ++a) u_out[a] = (j[a] + 0.5 * F[a]) / rho;
+}
+
+/* One cell's collision (Eq. 3 with Eq. 5 or TRT): f -> fs. */
+void orc_collide(const orc_problem *p, const double *f, double *fs) {
+    int q = p->q;
+    double rho, u[3], feq[27], S[27];
+    orc_moments(q, f, p->force, &rho, u);
+    orc_equilibrium(q, rho, u, feq);
+    orc_guo_source(q, u, p->force, S);
+    double wp = p->omega_plus;
+    if (p->op == ORC_SRT) {
+        for (int i = 0; i < q; ++i)
+            fs[i] = f[i] - wp * (f[i] - feq[i]) + (1.0 - 0.5 * wp) * S[i];
+        return;
+    }
+    double wm = p->omega_minus;
+    for (int i = 0; i < q; ++i) {
+        int b = inverse(q, i);
+        double fp = 0.5 * (f[i] + f[b]), fm = 0.5 * (f[i] - f[b]);
+        double ep = 0.5 * (feq[i] + feq[b]), em = 0.5 * (feq[i] - feq[b]);
+        double sp = 0.5 * (S[i] + S[b]), sm = 0.5 * (S[i] - S[b]);
+        fs[i] = f[i] - wp * (fp - ep) - wm * (fm - em) + (1.0 - 0.5 * wp) * sp +
+                (1.0 - 0.5 * wm) * sm;
+    }
+}
+
+/* Value a boundary link hands to the fluid cell: the PDF of direction r
+ * that re-enters the cell after its own post-collision PDF of direction
+ * inverse(r) (value `src`) hit the boundary voxel.
+ *   wall:   src                              (halfway bounce-back)
+ *   inlet:  src + 6 w_r rho0 (c_r . u_w)      (Ladd moving wall, rho0 = 1)
+ *   outlet: -src + 2 w_r rho_out             (linearised anti-bounce-back) */
+static double bc_value(const orc_problem *p, int type, double src, int r, const double *uw) {
+    double w = weight(p->q, r);
+    if (type == ORC_INLET) {
+        double cu = VEL[r][0] * uw[0] + VEL[r][1] * uw[1] + VEL[r][2] * uw[2];
+        return src + 6.0 * w * cu;
+    }
+    if (type == ORC_OUTLET) return -src + 2.0 * w * p->rho_out;
+    return src;
+}
+
+/* ------------------------------------------------------------ geometry */
+
+static int64_t nvox(const orc_problem *p) { return (int64_t)p->nx * p->ny * p->nz; }
+
+/* Neighbour voxel of (x,y,z) displaced by d: returns its linear id, or -1
+ * when it leaves the box through a non-periodic face (treated as a wall). */
+static int64_t neighbour(const orc_problem *p, int x, int y, int z, int dx, int dy, int dz) {
+    int n[3] = {x + dx, y + dy, z + dz};
+    int dim[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 0 || n[a] >= dim[a]) {
+            if (!(p->periodic >> a & 1u)) return -1;
+            n[a] = (n[a] + dim[a]) % dim[a];
+        }
+    }
+    return (int64_t)n[0] + (int64_t)p->nx * ((int64_t)n[1] + (int64_t)p->ny * n[2]);
+}
+
+static int type_of(const orc_problem *p, int64_t v) { return v < 0 ? ORC_WALL : p->flags[v]; }
+
+/* Rank of each inlet voxel among inlet voxels in ascending voxel order. */
+static int64_t *inlet_rank(const orc_problem *p) {
+    int64_t n = nvox(p);
+    int64_t *r = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t c = 0;
+    for (int64_t v = 0; v < n; ++v) r[v] = (p->flags[v] == ORC_INLET) ? c++ : -1;
+    return r;
+}
+
+static const double ZERO3[3] = {0.0, 0.0, 0.0};
+static const double *inlet_velocity(const orc_problem *p, const int64_t *rank, int64_t v) {
+    if (!p->inlet_u || v < 0 || rank[v] < 0) return ZERO3;
+    return p->inlet_u + 3 * rank[v];
+}
+
+/* ------------------------------------------------------- dense stepping */
+
+/* f: Q x N array (direction-major), all voxels; only fluid voxels are
+ * meaningful.  Initialises fluid voxels to f^eq(rho, u) (rho, u per voxel;
+ * NULL means the rest state rho = 1, u = 0). */
+void orc_dense_init(const orc_problem *p, const double *rho, const double *u, double *f) {
+    int64_t n = nvox(p);
+    for (int64_t v = 0; v < n; ++v) {
+        double r = rho ? rho[v] : 1.0;
+        double uv[3] = {u ? u[3 * v] : 0.0, u ? u[3 * v + 1] : 0.0, u ? u[3 * v + 2] : 0.0};
+        double feq[27];
+        orc_equilibrium(p->q, r, uv, feq);
+        for (int i = 0; i < p->q; ++i) f[(int64_t)i * n + v] = p->flags[v] == ORC_FLUID ? feq[i] : 0.0;
+    }
+}
+
+/* `steps` two-grid push steps: collide every fluid voxel of A, push each
+ * post-collision PDF to its neighbour in B (or reflect it at a boundary),
+ * then swap.  Result is left in f. */
+int orc_dense_run(const orc_problem *p, double *f, int steps) {
+    int64_t n = nvox(p);
+    int q = p->q;
+    double *B = (double *)malloc(sizeof(double) * (size_t)(q * n > 0 ? q * n : 1));
+    if (!B) return -1;
+    memcpy(B, f, sizeof(double) * (size_t)(q * n));
+    int64_t *rank = inlet_rank(p);
+    double *A = f;
+    for (int t = 0; t < steps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (int64_t v = 0; v < n; ++v) {
+            if (p->flags[v] != ORC_FLUID) continue;
+            int x = (int)(v % p->nx), y = (int)((v / p->nx) % p->ny), z = (int)(v / ((int64_t)p->nx * p->ny));
+            double fl[27], fs[27];
+            for (int i = 0; i < q; ++i) fl[i] = A[(int64_t)i * n + v];
+            orc_collide(p, fl, fs);
+            for (int i = 0; i < q; ++i) {
+                int64_t nb = neighbour(p, x, y, z, VEL[i][0], VEL[i][1], VEL[i][2]);
+                int ty = type_of(p, nb);
+                if (ty == ORC_FLUID) {
+                    B[(int64_t)i * n + nb] = fs[i];
+                } else {
+                    int r = inverse(q, i);
+                    B[(int64_t)r * n + v] = bc_value(p, ty, fs[i], r, inlet_velocity(p, rank, nb));
+                }
+            }
+        }
+        double *tmp = A; A = B; B = tmp;
+    }
+    if (A != f) {
+        memcpy(f, A, sizeof(double) * (size_t)(q * n));
+        B = A;
+    }
+    free(B);
+    free(rank);
+    return 0;
+}
+
+/* rho, u (Guo-corrected) per voxel; non-fluid voxels get rho = 0, u = 0. */
+void orc_dense_macroscopic(const orc_problem *p, const double *f, double *rho, double *u) {
+    int64_t n = nvox(p);
+    for (int64_t v = 0; v < n; ++v) {
+        if (p->flags[v] != ORC_FLUID) {
+            rho[v] = 0.0;
+            u[3 * v] = u[3 * v + 1] = u[3 * v + 2] = 0.0;
+            continue;
+        }
+        double fl[27];
+        for (int i = 0; i < p->q; ++i) fl[i] = f[(int64_t)i * n + v];
+        orc_moments(p->q, fl, p->force, &rho[v], &u[3 * v]);
+    }
+}
+
+/* ------------------------------------------------------- sparse indexing */
+
+/* Compacted fluid-cell order (Sec. 3.1): fluid voxels numbered in
+ * ascending linear voxel id (lexicographic, x fastest).  cell_id[v] = k or
+ * -1; cell_voxel[k] = v.  Returns N_F. */
+int64_t orc_compact(const orc_problem *p, int32_t *cell_id, int32_t *cell_voxel) {
+    int64_t n = nvox(p), k = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (p->flags[v] == ORC_FLUID) {
+            cell_id[v] = (int32_t)k;
+            cell_voxel[k] = (int32_t)v;
+            ++k;
+        } else {
+            cell_id[v] = -1;
+        }
+    }
+    return k;
+}
+
+#define ORC_PAD INT32_MIN
+
+/* Pull index-list (Sec. 3.1, Sec. 3.1.1).  Row r = i-1 for i = 1..Q-1,
+ * column k, stride S (>= N_F):
+ *   fluid neighbour x_k - c_i      -> i*S + cell_id(neighbour)
+ *   wall (or outside, non-periodic)-> inverse(i)*S + k      (same cell, inverse dir)
+ *   inlet / outlet voxel           -> -(b+1), b = running link number in
+ *                                     (k, i) order
+ *   padding columns k >= N_F       -> INT32_MIN
+ * Link table (n_bc entries, up to max_bc written): cell, direction,
+ * boundary type, and the inlet velocity of the boundary voxel.
+ * Returns the number of boundary links. */
+int64_t orc_pull_list(const orc_problem *p, const int32_t *cell_id, const int32_t *cell_voxel,
+                      int64_t nf, int64_t S, int32_t *P, int32_t *bc_cell, int32_t *bc_dir,
+                      int32_t *bc_type, double *bc_u, int64_t max_bc) {
+    int q = p->q;
+    int64_t nb_links = 0;
+    int64_t *rank = inlet_rank(p);
+    for (int i = 1; i < q; ++i)
+        for (int64_t k = nf; k < S; ++k) P[(int64_t)(i - 1) * S + k] = ORC_PAD;
+    for (int64_t k = 0; k < nf; ++k) {
+        int64_t v = cell_voxel[k];
+        int x = (int)(v % p->nx), y = (int)((v / p->nx) % p->ny), z = (int)(v / ((int64_t)p->nx * p->ny));
+        for (int i = 1; i < q; ++i) {
+            int64_t nb = neighbour(p, x, y, z, -VEL[i][0], -VEL[i][1], -VEL[i][2]);
+            int ty = type_of(p, nb);
+            int32_t val;
+            if (ty == ORC_FLUID) {
+                val = (int32_t)((int64_t)i * S + cell_id[nb]);
+            } else if (ty == ORC_WALL) {
+                val = (int32_t)((int64_t)inverse(q, i) * S + k);
+            } else {
+                if (nb_links < max_bc) {
+                    bc_cell[nb_links] = (int32_t)k;
+                    bc_dir[nb_links] = i;
+                    bc_type[nb_links] = ty;
+                    const double *uw = inlet_velocity(p, rank, nb);
+                    for (int a = 0; a < 3; ++a) bc_u[3 * nb_links + a] = uw[a];
+                }
+                val = (int32_t)(-(nb_links + 1));
+                ++nb_links;
+            }
+            P[(int64_t)(i - 1) * S + k] = val;
+        }
+    }
+    free(rank);
+    return nb_links;
+}
+
+/* ---------------------------------------------------- sparse stepping */
+
+/* Two-grid PULL stepping over the PDF-list (Q x S, slot i*S + k):
+ * collide every cell into C, then f_i(k) <- C[P(i,k)] for fluid/wall
+ * links and the boundary value of C[inverse(i)*S + k] for inlet/outlet
+ * links.  Uses the same per-cell arithmetic as orc_dense_run, so the two
+ * agree bit for bit. */
+int orc_sparse_run(const orc_problem *p, const int32_t *P, int64_t nf, int64_t S,
+                   const int32_t *bc_type, const double *bc_u, double *f, int steps) {
+    int q = p->q;
+    double *C = (double *)malloc(sizeof(double) * (size_t)(q * S > 0 ? q * S : 1));
+    if (!C) return -1;
+    for (int t = 0; t < steps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (int64_t k = 0; k < nf; ++k) {
+            double fl[27], fs[27];
+            for (int i = 0; i < q; ++i) fl[i] = f[(int64_t)i * S + k];
+            orc_collide(p, fl, fs);
+            for (int i = 0; i < q; ++i) C[(int64_t)i * S + k] = fs[i];
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t k = 0; k < nf; ++k) {
+            f[k] = C[k];
+            for (int i = 1; i < q; ++i) {
+                int32_t e = P[(int64_t)(i - 1) * S + k];
+                if (e >= 0) {
+                    f[(int64_t)i * S + k] = C[e];
+                } else {
+                    int64_t b = -(int64_t)e - 1;
+                    int r = inverse(q, i);
+                    f[(int64_t)i * S + k] =
+                        bc_value(p, bc_type[b], C[(int64_t)r * S + k], i, bc_u + 3 * b);
+                }
+            }
+        }
+    }
+    free(C);
+    return 0;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

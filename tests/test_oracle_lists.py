@@ -1,0 +1,159 @@
+"""Oracle pins for the sparse data structure (Sec. 3.1, 3.1.1): the compacted
+cell order and the pull index-list, against brute force written here in pure
+Python and against structural invariants; plus bitwise equality of the sparse
+pull stepper with the dense push stepper on tiny domains."""
+import numpy as np
+import pytest
+
+import geometry as G
+import oracle as O
+
+# Directions written out again for the brute force (independent of the
+# oracle's C table); the test checks the two agree.
+DIRS19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+          (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1),
+          (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+DIRS27 = DIRS19 + [(1, 1, 1), (-1, -1, -1), (1, 1, -1), (-1, -1, 1), (1, -1, 1), (-1, 1, -1),
+                   (-1, 1, 1), (1, -1, -1)]
+
+
+def brute_force_lists(g, q):
+    dirs = DIRS19 if q == 19 else DIRS27
+    nz, ny, nx = g.flags.shape
+    fl = g.flags
+    order = []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if fl[z, y, x] == G.FLUID:
+                    order.append((x, y, z))
+    index = {v: k for k, v in enumerate(order)}
+    nf = len(order)
+    S = (nf + 127) // 128 * 128
+    P = np.full((q - 1, S), np.iinfo(np.int32).min, np.int64)
+    links = []
+    for k, (x, y, z) in enumerate(order):
+        for i in range(1, q):
+            cx, cy, cz = dirs[i]
+            nbr = [x - cx, y - cy, z - cz]
+            outside = False
+            for a, n in enumerate((nx, ny, nz)):
+                if nbr[a] < 0 or nbr[a] >= n:
+                    if g.periodic >> a & 1:
+                        nbr[a] %= n
+                    else:
+                        outside = True
+            inv = dirs.index((-cx, -cy, -cz))
+            t = G.WALL if outside else fl[nbr[2], nbr[1], nbr[0]]
+            if t == G.FLUID:
+                P[i - 1, k] = i * S + index[tuple(nbr)]
+            elif t == G.WALL:
+                P[i - 1, k] = inv * S + k
+            else:
+                P[i - 1, k] = -(len(links) + 1)
+                links.append((k, i, int(t)))
+    return order, S, P, links
+
+
+def _mixed_geometry(seed):
+    g = G.random_solids((5, 4, 6), 0.3, seed, periodic=0b010)
+    f = g.flags
+    f[:, :, 0] = np.where(f[:, :, 0] == G.FLUID, G.INLET, f[:, :, 0])
+    f[:, :, -1] = np.where(f[:, :, -1] == G.FLUID, G.OUTLET, f[:, :, -1])
+    n_in = int(np.count_nonzero(f == G.INLET))
+    g.inlet_u = np.random.default_rng(seed).uniform(-0.05, 0.05, (n_in, 3))
+    return g
+
+
+CASES = [
+    ("periodic", lambda s: G.random_solids(4, 0.35, s, periodic=7)),
+    ("walled", lambda s: G.random_solids((4, 5, 3), 0.3, s, periodic=0)),
+    ("mixed_bc", _mixed_geometry),
+]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("name,make", CASES)
+def test_lists_match_brute_force(q, name, make):
+    c, _, _ = O.stencil(q)
+    assert [tuple(v) for v in c] == (DIRS19 if q == 19 else DIRS27)
+    for seed in range(3):
+        g = make(seed)
+        p = O.Problem.from_geometry(g, q=q)
+        L = O.pull_list(p)
+        order, S, P, links = brute_force_lists(g, q)
+        nz, ny, nx = g.flags.shape
+        assert L.n_fluid == len(order) and L.stride == S
+        assert np.array_equal(L.cell_voxel, [x + nx * (y + ny * z) for x, y, z in order])
+        assert np.array_equal(L.P, P)
+        assert [(int(a), int(b), int(t)) for a, b, t in zip(L.bc_cell, L.bc_dir, L.bc_type)] == links
+        # cell_id is the inverse of cell_voxel
+        assert np.array_equal(L.cell_id[L.cell_voxel], np.arange(L.n_fluid))
+        assert np.count_nonzero(L.cell_id >= 0) == L.n_fluid
+
+
+def _aa_read_slot(P, i, k, S, inv):
+    """AA odd-step read slot R(i,k): the pull entry with its row flipped
+    between i and inverse(i)."""
+    e = int(P[i - 1, k])
+    row = e // S
+    other = inv[i] if row == i else i
+    return other * S + (e - row * S)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_list_invariants_on_sphere_packing(q):
+    g = G.relaxed_spheres()          # 32^3, r = 4, phi ~ 0.5
+    p = O.Problem.from_geometry(g, q=q)
+    L = O.pull_list(p)
+    S, nf, P = L.stride, L.n_fluid, L.P
+    _, _, inv = O.stencil(q)
+    assert nf == np.count_nonzero(g.flags == G.FLUID)
+    assert P.shape == (q - 1, S)                       # N_F (Q-1) entries + padding
+    assert np.all(P[:, nf:] == O.PAD)
+    rows = P[:, :nf] // S
+    cols = P[:, :nf] - rows * S
+    for i in range(1, q):
+        r, cc = rows[i - 1], cols[i - 1]
+        fluid = r == i
+        wall = r == inv[i]
+        assert np.all(fluid | wall)
+        # no-slip links pull the same cell's inverse direction (Sec. 3.1.1)
+        assert np.array_equal(cc[wall], np.arange(nf)[wall])
+        # reciprocity: if k pulls direction i from n, n pulls inverse(i) from k
+        ks = np.arange(nf)[fluid]
+        ns = cc[fluid]
+        back = P[inv[i] - 1, ns]
+        assert np.array_equal(back, inv[i] * S + ks)
+    # the AA odd-step read slots of all cells and directions 1..Q-1 are a
+    # permutation of the non-centre slots: every slot read (and written) once
+    slots = np.concatenate([[_aa_read_slot(P, i, k, S, inv) for k in range(nf)]
+                            for i in range(1, q)])
+    expect = np.concatenate([i * S + np.arange(nf) for i in range(1, q)])
+    assert np.array_equal(np.sort(slots), np.sort(expect))
+
+
+SPARSE_DENSE = [
+    ("periodic_srt", lambda: G.random_solids(8, 0.3, 11, periodic=7), O.SRT),
+    ("walled_trt", lambda: G.random_solids(8, 0.25, 12, periodic=0b011, walls_z=True), O.TRT),
+    ("mixed_bc_trt", lambda: _mixed_geometry(13), O.TRT),
+]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("name,make,op", SPARSE_DENSE)
+def test_sparse_equals_dense_bitwise(q, name, make, op):
+    g = make()
+    p = O.Problem.from_geometry(g, q=q, op=op, force=(1e-5, -2e-6, 3e-6))
+    rng = np.random.default_rng(5)
+    n = p.n
+    rho = 1.0 + rng.uniform(-0.01, 0.01, n)
+    u = rng.uniform(-0.02, 0.02, (n, 3))
+    f0 = O.dense_init(p, rho, u)
+    L = O.pull_list(p)
+    fd = O.dense_run(p, f0, 10)
+    fs = O.sparse_run(p, L, O.sparse_from_dense(L, f0), 10)
+    got = fs[:, :L.n_fluid]
+    want = fd[:, L.cell_voxel]
+    assert np.array_equal(got, want)          # bit for bit
+    assert not np.array_equal(want, f0[:, L.cell_voxel])
