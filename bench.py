@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse AA lattice Boltzmann hot path on GB300.
+
+Workload (default): the 256^3 porosity sweep -- periodic Boolean sphere
+packings, radii U(6, 12), porosity 0.3 / 0.5 / 0.7 / 0.9 (seeds 11-14), D3Q19
+TRT (magic 3/16, tau 0.8), body force 1e-6 along x, FP32 shifted PDFs.
+One benchmark step = `--lbm-steps` (default 100, even) LBM time steps, i.e.
+alternating even/odd AA kernels, on each of the four domains.  The metric is
+fluid lattice updates per second (MFLUPS) over all four domains; each domain's
+PDF-list (>= 0.38 GB) exceeds the 129 MB L2, so no L2 flush is needed.
+
+Also measured in the same run and added to the JSON line: per-porosity MFLUPS
+and achieved HBM GB/s of each kernel against the measured copy peak, the dense
+direct-addressing comparator, the FP16-storage form, memory per fluid cell,
+an end-to-end solve through the public API from host buffers, and the FP64
+oracle on the host cores as a CPU baseline.
+
+`--impl reference` times the FP64 CPU oracle (a plain dense two-grid push
+LBM) on the host cores, on a bounded sample of the same workload.
+
+Multi-GPU: domains are independent, so every rank runs its own replica of
+the workload (weak scaling, no data-path collective)."""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fluid lattice updates/s (MFLUPS), D3Q19 TRT sparse AA, FP32"
+UNIT = "MFLUPS"
+POROSITIES = (0.3, 0.5, 0.7, 0.9)
+SEEDS = {0.3: 11, 0.5: 12, 0.7: 13, 0.9: 14}
+N = 256
+FORCE = (1e-6, 0.0, 0.0)
+OMEGA = 1.0 / 0.8
+MAGIC = 3.0 / 16.0
+Q = 19
+B_IDX = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lbm-steps", type=int, default=100, help="LBM time steps per benchmark step (even)")
+    ap.add_argument("--porosities", default=",".join(str(p) for p in POROSITIES))
+    ap.add_argument("--size", type=int, default=N)
+    ap.add_argument("--no-extras", action="store_true", help="skip dense / FP16 / e2e / CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    a = ap.parse_args()
+    if a.lbm_steps % 2:
+        raise SystemExit("--lbm-steps must be even (whole AA pairs)")
+    a.porosities = tuple(float(x) for x in a.porosities.split(","))
+    return a
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def geometry_for(phi, n):
+    import geometry as G
+    return G.boolean_spheres(n, phi, SEEDS.get(phi, 10 + int(phi * 10)))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j]})
+        power = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------- our arm
+def algorithmic_bytes(nf, b_pdf, q=Q, parity=0):
+    """AA access model (Table 2, Sec. 5.1): even 2Q B_pdf, odd 2Q B_pdf + (Q-1) B_idx per cell."""
+    return nf * (2 * q * b_pdf + (0 if parity == 0 else (q - 1) * B_IDX))
+
+
+def run_ours(a, rank, world):
+    import torch
+    import paper_2408_06880_gb300 as P
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    peak, peak_kind = load_peaks()
+    doms = []
+    for phi in a.porosities:
+        g = geometry_for(phi, a.size)
+        d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+                     stream=stream)
+        doms.append((phi, g, d))
+    half = a.lbm_steps // 2
+
+    def one_step(events=None):
+        for j, (_, _, d) in enumerate(doms):
+            for _ in range(half):
+                if events is not None:
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    e[0].record(stream)
+                    d.step(1)
+                    e[1].record(stream)
+                    d.step(1)
+                    e[2].record(stream)
+                    events[j].append(e)
+                else:
+                    d.step(2)
+
+    for _ in range(a.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    events = [[] for _ in doms]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(a.steps):
+        one_step(events)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    updates_rank = sum(d.n_fluid for _, _, d in doms) * a.lbm_steps * a.steps
+    value = updates_rank * world / (elapsed_ms / 1e3) / 1e6
+
+    # per-kernel durations from the events recorded on the launching stream
+    per = []
+    tot = {0: [0.0, 0.0], 1: [0.0, 0.0]}     # parity -> [bytes, ms]
+    for j, (phi, g, d) in enumerate(doms):
+        ev_ms = [e[0].elapsed_time(e[1]) for e in events[j]]
+        od_ms = [e[1].elapsed_time(e[2]) for e in events[j]]
+        nf = d.n_fluid
+        be, bo = algorithmic_bytes(nf, 4, parity=0), algorithmic_bytes(nf, 4, parity=1)
+        me, mo = float(np.mean(ev_ms)), float(np.mean(od_ms))
+        tot[0][0] += be * len(ev_ms)
+        tot[0][1] += sum(ev_ms)
+        tot[1][0] += bo * len(od_ms)
+        tot[1][1] += sum(od_ms)
+        per.append({"porosity": phi, "n_fluid": nf, "achieved_porosity": round(g.porosity, 4),
+                    "mflups": round(2 * nf / ((me + mo) / 1e3) / 1e6, 1),
+                    "even_ms": round(me, 4), "odd_ms": round(mo, 4),
+                    "even_gbs": round(be / me / 1e6, 1), "odd_gbs": round(bo / mo / 1e6, 1),
+                    "pair_gbs": round((be + bo) / (me + mo) / 1e6, 1),
+                    "pair_frac": round((be + bo) / (me + mo) / 1e6 / peak, 4),
+                    "bytes_per_cell": round(d.memory_bytes() / nf, 2)})
+    dom_par = 1 if tot[1][1] >= tot[0][1] else 0
+    achieved = tot[dom_par][0] / tot[dom_par][1] / 1e6
+    kname = "aa_odd_kernel" if dom_par else "aa_even_kernel"
+    n_launch = len(doms) * a.lbm_steps * a.steps
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic_for(kname, doms),
+                "algorithmic_bytes_per_launch": round(tot[dom_par][0] / (n_launch / 2)),
+                "both_kernels": {"even_gbs": round(tot[0][0] / tot[0][1] / 1e6, 1),
+                                 "odd_gbs": round(tot[1][0] / tot[1][1] / 1e6, 1),
+                                 "even_share": round(tot[0][1] / (tot[0][1] + tot[1][1]), 3)}}
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": round(elapsed_ms / a.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{a.size}^3 periodic Boolean sphere packings, porosity "
+                                  f"{'/'.join(str(p) for p in a.porosities)}, D3Q19 TRT magic 3/16, tau 0.8, "
+                                  f"F=1e-6 x, FP32 PDFs",
+                      "lbm_steps_per_step": a.lbm_steps, "domains": len(doms),
+                      "l2": "inputs larger than L2 (PDF-list >= 0.38 GB per domain), no flush",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "roofline": roofline, "per_porosity": per, "clocks": clk, "gpu_launches": n_launch}
+    if not a.no_extras and rank == 0:
+        out["dense"] = bench_dense(a, P, stream, peak)
+        out["fp16"] = bench_storage(a, P, stream, P.FP16, per)
+        out["e2e"] = bench_e2e(a, P)
+        if world == 1:
+            out["cpu_baseline"] = cpu_baseline(a)
+    for _, _, d in doms:
+        d.close()
+    return out
+
+
+def traffic_for(kname, doms):
+    """DRAM bytes per launch from the committed ncu summary, scaled by cells,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_digest") != kernel_digest():
+        return None
+    per_cell = t.get("kernels", {}).get(kname, {}).get("dram_bytes_per_cell")
+    if per_cell is None:
+        return None
+    nf = np.mean([d.n_fluid for _, _, d in doms])
+    return round(per_cell * nf)
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for name in ("common.cuh", "aa_kernels.cuh", "aa_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_2408_06880_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def bench_dense(a, P, stream, peak, pairs=10):
+    """Dense direct-addressing comparator on the same geometries (fluid MFLUPS)."""
+    import torch
+    res = []
+    for phi in a.porosities:
+        g = geometry_for(phi, a.size)
+        d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+                     layout=P.DENSE, stream=stream)
+        d.step(4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(2 * pairs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (2 * pairs)
+        nf = d.n_fluid
+        res.append({"porosity": phi, "mflups": round(nf / (ms / 1e3) / 1e6, 1),
+                    "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)})
+        d.close()
+    return res
+
+
+def bench_storage(a, P, stream, storage, per32, pairs=20):
+    import torch
+    res = []
+    for phi, p32 in zip(a.porosities, per32):
+        g = geometry_for(phi, a.size)
+        d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+                     storage=storage, scale_exp=P.auto_scale_exp(1e-3), stream=stream)
+        d.step(4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(2 * pairs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (2 * pairs)
+        m = d.n_fluid / (ms / 1e3) / 1e6
+        res.append({"porosity": phi, "mflups": round(m, 1), "vs_fp32": round(m / p32["mflups"], 3),
+                    "bytes_per_cell": round(d.memory_bytes() / d.n_fluid, 2)})
+        d.close()
+    return res
+
+
+def bench_e2e(a, P, pairs=50):
+    """A whole solve through the public API from HOST buffers: create from the
+    host flag array (H2D), `pairs` AA pairs each followed by a D2H read of the
+    FP64 domain sums, free.  Wall-clock MFLUPS."""
+    phi = 0.5 if 0.5 in a.porosities else a.porosities[0]
+    g = geometry_for(phi, a.size)
+    t = time.perf_counter()
+    d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE)
+    for _ in range(pairs):
+        d.step(2)
+        s = d.reduce()
+    nf = d.n_fluid
+    d.close()
+    wall = time.perf_counter() - t
+    return {"value": round(2 * pairs * nf / wall / 1e6, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(g.flags.size // pairs), "d2h_bytes_per_step": 40,
+            "what": f"create from host flags + {pairs} AA pairs with a host read of the 5 FP64 sums "
+                    f"after each pair + free, porosity {phi}; H2D bytes amortised over the pairs",
+            "final_sum_ux": float(s[4])}
+
+
+def cpu_baseline(a):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded
+    sample: the porosity-0.5 domain, repeated 2-step runs until the budget."""
+    import oracle as O
+    phi = 0.5 if 0.5 in a.porosities else a.porosities[0]
+    g = geometry_for(phi, a.size)
+    p = O.Problem.from_geometry(g, q=Q, op=O.TRT, omega_plus=OMEGA, magic=MAGIC, force=FORCE)
+    f = O.dense_init(p)
+    nf = int(np.count_nonzero(g.flags == 0))
+    steps, t = 0, time.perf_counter()
+    while True:
+        f = O.dense_run(p, f, 2)
+        steps += 2
+        if time.perf_counter() - t >= a.cpu_seconds:
+            break
+    wall = time.perf_counter() - t
+    return {"value": round(nf * steps / wall / 1e6, 3), "unit": UNIT, "cores": O.max_threads(),
+            "kind": "oracle", "sample": f"dense FP64 push oracle, {a.size}^3 porosity {phi} domain, "
+                                        f"{steps} LBM steps ({wall:.1f} s)"}
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(a):
+    """The FP64 CPU oracle on the host cores; each benchmark step is one
+    AA-pair-equivalent (2 dense two-grid steps) on the porosity-0.5 domain."""
+    import oracle as O
+    phi = 0.5 if 0.5 in a.porosities else a.porosities[0]
+    g = geometry_for(phi, a.size)
+    p = O.Problem.from_geometry(g, q=Q, op=O.TRT, omega_plus=OMEGA, magic=MAGIC, force=FORCE)
+    f = O.dense_init(p)
+    nf = int(np.count_nonzero(g.flags == 0))
+    for _ in range(a.warmup):
+        f = O.dense_run(p, f, 2)
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        f = O.dense_run(p, f, 2)
+    wall = time.perf_counter() - t
+    v = 2 * nf * a.steps / wall / 1e6
+    sample = f"dense FP64 push oracle, {a.size}^3 porosity {phi} domain, 2 LBM steps per benchmark step"
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(wall / a.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{a.size}^3 periodic Boolean sphere packing, porosity {phi}, D3Q19 TRT, "
+                                   f"F=1e-6 x (CPU oracle sample)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(a)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out = run_ours(a, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

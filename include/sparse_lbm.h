@@ -1,0 +1,205 @@
+/*
+ * sparse_lbm.h -- C ABI of the GB300 sparse (indirect-addressing) lattice
+ * Boltzmann library.
+ *
+ * The library implements the sparse data structure of Suffa et al., "Architecture
+ * Specific Generation of Large Scale Lattice Boltzmann Methods for Sparse Complex
+ * Geometries" (Sec. 3.1): only fluid cells are stored, in a compacted
+ * direction-major PDF-list of Q rows, plus a pull index-list of Q-1 rows that
+ * replaces the lost neighbourhood information, with no-slip and periodic
+ * boundaries folded into the list (Sec. 3.1.1).  Time stepping uses the in-place
+ * AA pattern (Sec. 5.1): a cell-local "even" step and an index-driven "odd" step
+ * on one PDF field.  The collision is SRT (Eq. 5) or TRT with the second-order
+ * equilibrium (Eq. 6) and a Guo body force.
+ *
+ * Conventions shared by every call
+ *   - Every call returns an slbm_status; nothing aborts or throws across the ABI.
+ *     On failure, sparse_lbm_last_error() returns a thread-local message.
+ *   - Device work is enqueued on the stream given at creation (a cudaStream_t
+ *     passed as void*; NULL makes the library create a blocking stream of its
+ *     own, which orders with the legacy default stream).  Calls that return
+ *     host data synchronise that stream.
+ *   - Device memory is owned by the library (optionally obtained through the
+ *     caller's slbm_allocator).  Output buffers are owned by the caller.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns SLBM_ECUDA.
+ *   - Voxel ids are x + nx*(y + ny*z) (x fastest).  Flag values: 0 fluid,
+ *     1 no-slip wall, 2 velocity inlet, 3 pressure outlet.  A neighbour outside
+ *     the box along a non-periodic axis counts as a wall.
+ *   - Velocity-set order (part of the ABI; the index-list depends on it):
+ *       0:(0,0,0)  1:(1,0,0)  2:(-1,0,0)  3:(0,1,0)  4:(0,-1,0)  5:(0,0,1)
+ *       6:(0,0,-1) 7:(1,1,0)  8:(-1,-1,0) 9:(1,-1,0) 10:(-1,1,0) 11:(1,0,1)
+ *       12:(-1,0,-1) 13:(1,0,-1) 14:(-1,0,1) 15:(0,1,1) 16:(0,-1,-1)
+ *       17:(0,1,-1) 18:(0,-1,1), and for D3Q27 additionally 19:(1,1,1)
+ *       20:(-1,-1,-1) 21:(1,1,-1) 22:(-1,-1,1) 23:(1,-1,1) 24:(-1,1,-1)
+ *       25:(-1,1,1) 26:(1,-1,-1).  inverse(i) = i+1 for odd i, i-1 for even i>0.
+ */
+#ifndef SPARSE_LBM_H
+#define SPARSE_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slbm_domain slbm_t;     /* opaque domain handle */
+typedef struct slbm_pool slbm_pool_t;  /* opaque batch of domains */
+
+typedef enum {
+    SLBM_OK = 0,
+    SLBM_EINVAL = 1,        /* invalid argument (dims, omega, q, pointer, size) */
+    SLBM_ENOMEM = 2,        /* device allocation failed or budget exceeded */
+    SLBM_ECUDA = 3,         /* a CUDA runtime call failed / no device */
+    SLBM_EUNSUPPORTED = 4,  /* valid but not supported (e.g. Q*stride >= 2^31) */
+    SLBM_EDIVERGED = 5,     /* a reduction produced NaN/Inf or |u| > 0.3 */
+    SLBM_ETIMEOUT = 6,      /* a bounded device wait gave up */
+    SLBM_EABORTED = 7,      /* the host abort flag was raised */
+    SLBM_EDEVICE = 8        /* a device-side check latched an error (checked kernels) */
+} slbm_status;
+
+enum { SLBM_SRT = 0, SLBM_TRT = 1 };
+enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
+enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1 };
+enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
+enum { SLBM_ORDER_CELLS = 0, SLBM_ORDER_VOXELS = 1 };
+
+/* Problem description (Sec. 2 parameters, Sec. 3 geometry). */
+typedef struct {
+    int32_t nx, ny, nz;        /* voxel box, each >= 1 */
+    const uint8_t *flags;      /* HOST, nx*ny*nz flags (0..3), read during create only */
+    uint32_t periodic;         /* bit0 x, bit1 y, bit2 z */
+    int32_t q;                 /* 19 or 27 */
+    int32_t op;                /* SLBM_SRT or SLBM_TRT */
+    double omega_plus;         /* 1/tau in (0, 2) (Eq. 7) */
+    double trt_magic;          /* TRT magic parameter Lambda > 0; ignored for SRT */
+    double force[3];           /* constant body-force density (Guo) */
+    const float *inlet_u;      /* HOST, nullable: 3 floats per inlet voxel, ascending voxel id */
+    int64_t n_inlet_u;         /* entries (voxels) in inlet_u; must equal the inlet count */
+    double rho_out;            /* pressure-outlet density */
+    int32_t storage;           /* SLBM_FP32 / SLBM_FP16 / SLBM_BF16 shifted populations */
+    int32_t scale_exp;         /* FP16/BF16: stored value = (f_i - w_i) * 2^scale_exp, |.| <= 40 */
+    int32_t layout;            /* SLBM_LAYOUT_SPARSE (the method) or SLBM_LAYOUT_DENSE (comparator) */
+    int32_t reserved;          /* must be 0 */
+} slbm_desc;
+
+/* Optional device allocator.  alloc returns device memory (256-byte aligned)
+ * or NULL; free releases it.  Both are called on the creating thread only. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} slbm_allocator;
+
+typedef struct {
+    int64_t n_voxels;          /* nx*ny*nz */
+    int64_t n_fluid;           /* N_F, fluid cells (Eq. 8 numerator) */
+    int64_t stride;            /* S: PDF-list row stride, N_F rounded up to 128 (sparse) or N (dense) */
+    int64_t n_bc_links;        /* inlet/outlet links in the index-list */
+    int64_t device_bytes;      /* library-owned device memory held by the handle */
+    int64_t step;              /* time steps taken (the AA parity is step & 1) */
+    int32_t q, op, storage, layout, scale_exp, pad;
+} slbm_info;
+
+/* Build a domain from a voxel geometry (Sec. 3.1): copy the flags to the
+ * device, compact the fluid cells with a device prefix sum (lexicographic
+ * order, bit-identical to a sequential scan), build the pull index-list
+ * P(i,k) (Q-1 rows x stride int32; fluid neighbour x_k - c_i -> i*S + its
+ * cell, wall -> inverse(i)*S + k, inlet/outlet -> -(b+1) with b the link
+ * number in (k, i) order, padding columns -> INT32_MIN) and the boundary-link
+ * table, and initialise the rest state (rho = 1, u = 0; all shifted
+ * populations zero).  `stream` is a cudaStream_t or NULL.  On success *out
+ * owns all device memory of the domain.  Errors: SLBM_EINVAL (bad desc),
+ * SLBM_EUNSUPPORTED (Q*S >= 2^31), SLBM_ENOMEM, SLBM_ECUDA. */
+slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc, void *stream,
+                              slbm_t **out);
+
+/* Advance n >= 0 time steps (Eqs. 3-4 fused, AA pattern of Sec. 5.1): step t
+ * even -> cell-local collide writing each post-collision PDF into the inverse
+ * direction's slot; t odd -> read the index-list, gather through it, collide,
+ * scatter back to the slots read.  Asynchronous on the handle's stream. */
+slbm_status sparse_lbm_step(slbm_t *h, int32_t n);
+
+/* Same as sparse_lbm_step but replays a CUDA graph holding n launches
+ * (captured on first use for each (n, parity) and cached). */
+slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n);
+
+/* Macroscopic fields (Eq. 1 with the Guo half-force velocity) of the current
+ * state, at either AA parity.  rho: n floats; u: 3 x n floats, component-major
+ * (u_x of all cells, then u_y, then u_z).  order SLBM_ORDER_CELLS -> n = N_F
+ * in compacted order; SLBM_ORDER_VOXELS -> n = nx*ny*nz, zero off fluid.
+ * mem SLBM_MEM_DEVICE -> device pointers, asynchronous; SLBM_MEM_HOST -> host
+ * pointers, synchronous.  Either pointer may be NULL. */
+slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t order, int32_t mem);
+
+/* Domain sums in FP64, deterministic (fixed partition and order, independent
+ * of launch configuration): out[0] = sum(rho - 1), out[1..3] = sum rho*u,
+ * out[4] = sum u_x, over fluid cells.  mem selects a device or host pointer
+ * (host: synchronous).  Returns SLBM_EDIVERGED (after writing out) when a sum
+ * is not finite. */
+slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem);
+
+/* Set the state to the equilibrium of given fields (Eq. 6): rho (n floats)
+ * and u (3 x n, component-major) in cell or voxel order, device or host
+ * memory.  NULL rho means 1, NULL u means 0.  Resets the step counter to 0. */
+slbm_status sparse_lbm_init_equilibrium(slbm_t *h, const float *rho, const float *u,
+                                        int32_t order, int32_t mem);
+
+slbm_status sparse_lbm_info(const slbm_t *h, slbm_info *out);
+
+/* Copy the sparse lists to HOST buffers (any pointer may be NULL):
+ * cell_voxel[N_F]; index_rows[(Q-1)*S] (row r = direction r+1); link_cell,
+ * link_dir, link_type [n_bc_links]. Synchronous. Sparse layout only. */
+slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_t *index_rows,
+                                    int32_t *link_cell, int32_t *link_dir, int32_t *link_type);
+
+/* Checkpoint / resume: raw stored PDFs (Q x S elements of the storage type,
+ * bytes = Q*S*element size) plus the step counter, to or from HOST memory.
+ * A resumed run continues bit-for-bit like an uninterrupted one. */
+slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes);
+slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step);
+slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
+
+/* Launch shape used for a parity (0 even, 1 odd): threads per block (multiple
+ * of 32, <= 1024) and cells per thread (1, 2 or 4; odd step: 1 or 2).
+ * Chosen by the autotuner; defaults are 256 x 2 (even) and 256 x 1 (odd). */
+slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells);
+
+/* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch
+ * SLBM_EDEVICE instead of touching memory out of range; 0 = fast path. */
+slbm_status sparse_lbm_set_checked(slbm_t *h, int32_t on);
+
+/* Latched device error (0 none), synchronising the stream. Clears it. */
+slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code);
+
+/* Release everything; NULL is a no-op. */
+void sparse_lbm_free(slbm_t *h);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *sparse_lbm_last_error(void);
+
+/* ---- batching: many domains stepped by one persistent kernel ----------------
+ * A pool steps every member domain through one launch per time step: the
+ * members' compacted cell lists are concatenated through a device domain table
+ * (per-domain cell offset, stride, parity, rates, force, link table), so small
+ * domains share the GPU.  Members keep their own memory and handles; all must
+ * share q and storage.  Reductions are per member and bit-identical to
+ * sparse_lbm_reduce on the same state. */
+slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream,
+                             slbm_pool_t **out);
+slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot);
+slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot);
+/* k >= 0 steps on every member (each at its own parity); use_graph != 0
+ * replays a captured CUDA graph of the k launches. */
+slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph);
+/* out: 5 doubles per slot (capacity x 5), device or host; unused slots zero. */
+slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem);
+/* Persistent-kernel shape (threads per block, CTAs per SM; 0 = auto). */
+slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm);
+void slbm_pool_free(slbm_pool_t *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPARSE_LBM_H */

@@ -1,0 +1,57 @@
+// aa_launch.cuh -- host dispatch of the AA kernels for one stencil size.
+#pragma once
+
+#include "aa_kernels.cuh"
+#include "internal.h"
+
+namespace slbm {
+
+template <int Q, int ST>
+static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    T *pdf = reinterpret_cast<T *>(d.pdf.p);
+    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
+    if (nf == 0) return cudaSuccess;
+    const CollideParams p = d.collide_params();
+    const LaunchShape sh = d.shape[parity];
+    auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
+    if (parity == 0) {
+        switch (sh.cells) {
+            case 1: aa_even_kernel<Q, ST, 1><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p); break;
+            case 2: aa_even_kernel<Q, ST, 2><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p); break;
+            case 4: aa_even_kernel<Q, ST, 4><<<grid(4), sh.threads, 0, st>>>(pdf, S, nf, p); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
+    const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
+    const int32_t nl = (int32_t)d.n_links;
+    int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
+    const bool bc = nl > 0;
+    if (d.checked) {
+        if (bc) aa_odd_kernel<Q, ST, 1, true, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err);
+        else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err);
+        return cudaGetLastError();
+    }
+    switch (sh.cells * 2 + (bc ? 1 : 0)) {
+        case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
+        case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
+        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
+        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t launch_aa_step_q(const Domain &d, int parity, cudaStream_t st) {
+    switch (d.storage) {
+        case SLBM_FP32: return launch_aa_storage<Q, ST_F32>(d, parity, st);
+        case SLBM_FP16: return launch_aa_storage<Q, ST_F16>(d, parity, st);
+        case SLBM_BF16: return launch_aa_storage<Q, ST_BF16>(d, parity, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace slbm

@@ -1,0 +1,478 @@
+// api.cu -- the extern "C" entry points declared in include/sparse_lbm.h.
+//
+// Host orchestration only: validation, memory, streams, CUDA graphs and
+// copies.  Every arithmetic step of the method runs in the kernels of
+// lists.cu, aa_*.cu, macro.cu and dense.cu.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace slbm {
+
+static thread_local std::string g_msg;
+static thread_local slbm_status g_status = SLBM_OK;
+
+void set_error(slbm_status s, const std::string &msg) {
+    g_status = s;
+    g_msg = msg;
+}
+slbm_status last_status() { return g_status; }
+
+int Ctx::alloc(DevBuf &b, int64_t bytes) {
+    b.p = nullptr;
+    b.bytes = 0;
+    if (bytes <= 0) return 0;
+    void *p = nullptr;
+    if (hook) {
+        p = hook->alloc((size_t)bytes, hook->ctx);
+        if (!p) {
+            fail(SLBM_ENOMEM, "allocator hook returned NULL");
+            return -1;
+        }
+    } else {
+        const cudaError_t e = cudaMalloc(&p, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(SLBM_ENOMEM, (std::string("cudaMalloc: ") + cudaGetErrorString(e)).c_str());
+            return -1;
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    if (held) *held += bytes;
+    return 0;
+}
+
+void Ctx::release(DevBuf &b) {
+    if (b.p) {
+        if (hook) hook->free(b.p, hook->ctx);
+        else cudaFree(b.p);
+        if (held) *held -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int Ctx::check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return 0;
+    cudaGetLastError();
+    fail(SLBM_ECUDA, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+    return -1;
+}
+
+void Ctx::fail(slbm_status s, const char *msg) {
+    if (status == SLBM_OK) {
+        status = s;
+        set_error(s, msg);
+    }
+}
+
+CollideParams Domain::collide_params() const {
+    CollideParams p;
+    p.omega_p = (float)omega_p;
+    p.omega_m = (float)omega_m;
+    p.fx = (float)force[0];
+    p.fy = (float)force[1];
+    p.fz = (float)force[2];
+    const int s = storage == SLBM_FP32 ? 0 : scale_exp;
+    p.scale = std::ldexp(1.0f, s);
+    p.inv_scale = std::ldexp(1.0f, -s);
+    return p;
+}
+
+template <int Q>
+cudaError_t launch_aa_step_q(const Domain &d, int parity, cudaStream_t st);
+extern template cudaError_t launch_aa_step_q<19>(const Domain &, int, cudaStream_t);
+extern template cudaError_t launch_aa_step_q<27>(const Domain &, int, cudaStream_t);
+
+cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st) {
+    return d.q == 19 ? launch_aa_step_q<19>(d, parity, st) : launch_aa_step_q<27>(d, parity, st);
+}
+
+static cudaError_t launch_one_step(const Domain &d, int parity, cudaStream_t st) {
+    return d.layout == SLBM_LAYOUT_SPARSE ? launch_aa_step(d, parity, st) : launch_dense_step(d, parity, st);
+}
+
+static void drop_graphs(Domain &d) {
+    for (auto &kv : d.graphs) cudaGraphExecDestroy(kv.second);
+    d.graphs.clear();
+}
+
+static void release_all(Domain &d) {
+    Ctx cx = d.ctx();
+    DevBuf *bufs[] = {&d.pdf, &d.P, &d.cell_voxel, &d.link_cell, &d.link_dir, &d.link_type, &d.link_map,
+                      &d.mask, &d.red_partial, &d.red_out, &d.err};
+    for (DevBuf *b : bufs) cx.release(*b);
+}
+
+static slbm_status ok() {
+    g_status = SLBM_OK;
+    g_msg.clear();
+    return SLBM_OK;
+}
+
+static slbm_status err(slbm_status s, const std::string &m) {
+    set_error(s, m);
+    return s;
+}
+
+static slbm_status cuda_err(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return err(SLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace slbm
+
+using namespace slbm;
+
+extern "C" {
+
+const char *sparse_lbm_last_error(void) { return g_msg.c_str(); }
+
+slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc, void *stream, slbm_t **out) {
+    if (!desc || !out) return err(SLBM_EINVAL, "desc and out must be non-NULL");
+    *out = nullptr;
+    const slbm_desc &s = *desc;
+    if (s.nx < 1 || s.ny < 1 || s.nz < 1) return err(SLBM_EINVAL, "nx, ny, nz must be >= 1");
+    const int64_t N = (int64_t)s.nx * s.ny * s.nz;
+    if (N >= ((int64_t)1 << 31)) return err(SLBM_EUNSUPPORTED, "nx*ny*nz must be < 2^31");
+    if (!s.flags) return err(SLBM_EINVAL, "flags must be non-NULL");
+    if (s.q != 19 && s.q != 27) return err(SLBM_EINVAL, "q must be 19 or 27");
+    if (s.op != SLBM_SRT && s.op != SLBM_TRT) return err(SLBM_EINVAL, "op must be SRT (0) or TRT (1)");
+    if (!(s.omega_plus > 0.0 && s.omega_plus < 2.0)) return err(SLBM_EINVAL, "omega_plus must lie in (0, 2)");
+    if (s.op == SLBM_TRT && !(s.trt_magic > 0.0 && std::isfinite(s.trt_magic)))
+        return err(SLBM_EINVAL, "trt_magic must be > 0");
+    if (s.storage < SLBM_FP32 || s.storage > SLBM_BF16) return err(SLBM_EINVAL, "storage must be 0, 1 or 2");
+    if (s.scale_exp < -40 || s.scale_exp > 40) return err(SLBM_EINVAL, "scale_exp must lie in [-40, 40]");
+    if (s.layout != SLBM_LAYOUT_SPARSE && s.layout != SLBM_LAYOUT_DENSE) return err(SLBM_EINVAL, "bad layout");
+    if (s.reserved != 0) return err(SLBM_EINVAL, "reserved must be 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(s.force[a])) return err(SLBM_EINVAL, "force must be finite");
+    if (!(s.rho_out > 0.0 && std::isfinite(s.rho_out))) return err(SLBM_EINVAL, "rho_out must be > 0");
+    // host pass over the flags: range check, boundary presence, counts
+    int64_t n_fluid_host = 0, n_inlet = 0;
+    bool has_bc = false;
+    for (int64_t v = 0; v < N; ++v) {
+        const uint8_t f = s.flags[v];
+        if (f > 3) return err(SLBM_EINVAL, "flag values must be 0..3");
+        n_fluid_host += f == 0;
+        n_inlet += f == 2;
+        has_bc |= f >= 2;
+    }
+    if (s.inlet_u && s.n_inlet_u != n_inlet)
+        return err(SLBM_EINVAL, "n_inlet_u must equal the number of inlet voxels");
+    if (s.layout == SLBM_LAYOUT_DENSE && has_bc)
+        return err(SLBM_EUNSUPPORTED, "the dense comparator supports walls and periodic boundaries only");
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return err(SLBM_ECUDA, "no CUDA device available (there is no CPU fallback)");
+    }
+
+    slbm_t *h = new slbm_t();
+    Domain &d = h->d;
+    d.nx = s.nx;
+    d.ny = s.ny;
+    d.nz = s.nz;
+    d.periodic = s.periodic & 7u;
+    d.n_vox = N;
+    d.q = s.q;
+    d.op = s.op;
+    d.storage = s.storage;
+    d.layout = s.layout;
+    d.scale_exp = s.storage == SLBM_FP32 ? 0 : s.scale_exp;
+    d.omega_p = s.omega_plus;
+    d.magic = s.trt_magic;
+    d.omega_m = s.op == SLBM_TRT ? 1.0 / (s.trt_magic / (1.0 / s.omega_plus - 0.5) + 0.5) : s.omega_plus;
+    for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
+    d.rho_out = s.rho_out;
+    if (alloc) {
+        if (!alloc->alloc || !alloc->free) {
+            delete h;
+            return err(SLBM_EINVAL, "allocator needs alloc and free");
+        }
+        d.hook = *alloc;
+        d.has_hook = true;
+    }
+    if (stream) {
+        d.stream = (cudaStream_t)stream;
+    } else {
+        ce = cudaStreamCreate(&d.stream);
+        if (ce != cudaSuccess) {
+            delete h;
+            return cuda_err(ce, "cudaStreamCreate");
+        }
+        d.own_stream = true;
+    }
+    Ctx cx = d.ctx();
+    DevBuf flags;
+    int rc = cx.alloc(flags, N);
+    if (!rc) rc = cx.check(cudaMemcpyAsync(flags.p, s.flags, N, cudaMemcpyHostToDevice, d.stream), "flags H2D");
+    if (!rc) {
+        if (d.layout == SLBM_LAYOUT_SPARSE) {
+            rc = build_sparse_lists(cx, d, (const uint8_t *)flags.p, has_bc, s.inlet_u, s.n_inlet_u);
+            if (!rc && d.n_fluid != n_fluid_host) {
+                cx.fail(SLBM_ECUDA, "device compaction count disagrees with the host count");
+                rc = -1;
+            }
+        } else {
+            d.n_fluid = n_fluid_host;
+            d.S = (N + 127) / 128 * 128;
+            rc = build_dense_mask(cx, d, (const uint8_t *)flags.p);
+        }
+    }
+    const int64_t rows_bytes = (int64_t)d.q * d.S * d.bytes_per_pdf();
+    if (!rc) rc = cx.alloc(d.pdf, rows_bytes);
+    if (!rc && rows_bytes) rc = cx.check(cudaMemsetAsync(d.pdf.p, 0, rows_bytes, d.stream), "memset pdf");
+    if (!rc) rc = cx.alloc(d.red_partial, std::max<int64_t>(d.red_chunks(), 1) * 5 * sizeof(double));
+    if (!rc) rc = cx.alloc(d.red_out, 5 * sizeof(double));
+    if (!rc) rc = cx.alloc(d.err, sizeof(int32_t));
+    if (!rc) rc = cx.check(cudaMemsetAsync(d.err.p, 0, sizeof(int32_t), d.stream), "memset err");
+    if (!rc) rc = cx.check(cudaStreamSynchronize(d.stream), "create sync");
+    cx.release(flags);
+    if (rc) {
+        const slbm_status st = cx.status == SLBM_OK ? SLBM_ECUDA : cx.status;
+        const std::string m = g_msg;
+        release_all(d);
+        if (d.own_stream) cudaStreamDestroy(d.stream);
+        delete h;
+        return err(st, m);
+    }
+    *out = h;
+    return ok();
+}
+
+slbm_status sparse_lbm_step(slbm_t *h, int32_t n) {
+    if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
+    Domain &d = h->d;
+    for (int32_t t = 0; t < n; ++t) {
+        const cudaError_t e = launch_one_step(d, (int)(d.step & 1), d.stream);
+        if (e != cudaSuccess) return cuda_err(e, "step launch");
+        ++d.step;
+    }
+    return ok();
+}
+
+slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n) {
+    if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
+    if (n == 0) return ok();
+    Domain &d = h->d;
+    const std::pair<int, int> key(n, (int)(d.step & 1));
+    auto it = d.graphs.find(key);
+    if (it == d.graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(e, "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (int32_t t = 0; t < n && le == cudaSuccess; ++t) le = launch_one_step(d, (int)((d.step + t) & 1), d.stream);
+        e = cudaStreamEndCapture(d.stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_err(le, "launch during capture");
+        }
+        if (e != cudaSuccess) return cuda_err(e, "end capture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_err(e, "graph instantiate");
+        it = d.graphs.emplace(key, ex).first;
+    }
+    const cudaError_t e = cudaGraphLaunch(it->second, d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "graph launch");
+    d.step += n;
+    return ok();
+}
+
+slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t order, int32_t mem) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    if (order != SLBM_ORDER_CELLS && order != SLBM_ORDER_VOXELS) return err(SLBM_EINVAL, "bad order");
+    if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return err(SLBM_EINVAL, "bad mem");
+    Domain &d = h->d;
+    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox);
+    if (mem == SLBM_MEM_DEVICE) {
+        if (order == SLBM_ORDER_VOXELS) {   // zero the non-fluid entries first
+            if (rho && n) cudaMemsetAsync(rho, 0, n * sizeof(float), d.stream);
+            if (u && n) cudaMemsetAsync(u, 0, 3 * n * sizeof(float), d.stream);
+        }
+        const cudaError_t e = launch_macroscopic(d, rho, u, order, d.stream);
+        return e == cudaSuccess ? ok() : cuda_err(e, "macroscopic");
+    }
+    Ctx cx = d.ctx();
+    cx.held = nullptr;
+    DevBuf dr, du;
+    if ((rho && cx.alloc(dr, n * sizeof(float))) || (u && cx.alloc(du, 3 * n * sizeof(float))))
+        return err(cx.status, g_msg);
+    int rc = 0;
+    if (dr.p) rc |= cx.check(cudaMemsetAsync(dr.p, 0, n * sizeof(float), d.stream), "memset");
+    if (du.p) rc |= cx.check(cudaMemsetAsync(du.p, 0, 3 * n * sizeof(float), d.stream), "memset");
+    if (!rc) rc = cx.check(launch_macroscopic(d, (float *)dr.p, (float *)du.p, order, d.stream), "macroscopic");
+    if (!rc && dr.p)
+        rc = cx.check(cudaMemcpyAsync(rho, dr.p, n * sizeof(float), cudaMemcpyDeviceToHost, d.stream), "rho D2H");
+    if (!rc && du.p)
+        rc = cx.check(cudaMemcpyAsync(u, du.p, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, d.stream), "u D2H");
+    if (!rc) rc = cx.check(cudaStreamSynchronize(d.stream), "macroscopic sync");
+    cx.release(dr);
+    cx.release(du);
+    return rc ? err(cx.status, g_msg) : ok();
+}
+
+slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem) {
+    if (!h || !out) return err(SLBM_EINVAL, "null argument");
+    Domain &d = h->d;
+    if (mem == SLBM_MEM_DEVICE) {
+        const cudaError_t e = launch_reduce(d, out, d.stream);
+        return e == cudaSuccess ? ok() : cuda_err(e, "reduce");
+    }
+    if (mem != SLBM_MEM_HOST) return err(SLBM_EINVAL, "bad mem");
+    cudaError_t e = launch_reduce(d, (double *)d.red_out.p, d.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d.red_out.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "reduce");
+    for (int c = 0; c < 5; ++c)
+        if (!std::isfinite(out[c])) return err(SLBM_EDIVERGED, "domain sums are not finite");
+    return ok();
+}
+
+slbm_status sparse_lbm_init_equilibrium(slbm_t *h, const float *rho, const float *u, int32_t order, int32_t mem) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    if (order != SLBM_ORDER_CELLS && order != SLBM_ORDER_VOXELS) return err(SLBM_EINVAL, "bad order");
+    Domain &d = h->d;
+    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox);
+    Ctx cx = d.ctx();
+    cx.held = nullptr;
+    DevBuf dr, du;
+    const float *pr = rho, *pu = u;
+    int rc = 0;
+    if (mem == SLBM_MEM_HOST) {
+        if (rho && !rc) {
+            rc = cx.alloc(dr, n * sizeof(float));
+            if (!rc) rc = cx.check(cudaMemcpyAsync(dr.p, rho, n * sizeof(float), cudaMemcpyHostToDevice, d.stream), "H2D");
+            pr = (const float *)dr.p;
+        }
+        if (u && !rc) {
+            rc = cx.alloc(du, 3 * n * sizeof(float));
+            if (!rc) rc = cx.check(cudaMemcpyAsync(du.p, u, 3 * n * sizeof(float), cudaMemcpyHostToDevice, d.stream), "H2D");
+            pu = (const float *)du.p;
+        }
+    } else if (mem != SLBM_MEM_DEVICE) {
+        return err(SLBM_EINVAL, "bad mem");
+    }
+    if (!rc) rc = cx.check(launch_init_equilibrium(d, pr, pu, order, d.stream), "init");
+    if (!rc && mem == SLBM_MEM_HOST) rc = cx.check(cudaStreamSynchronize(d.stream), "init sync");
+    cx.release(dr);
+    cx.release(du);
+    if (rc) return err(cx.status, g_msg);
+    d.step = 0;
+    return ok();
+}
+
+slbm_status sparse_lbm_info(const slbm_t *h, slbm_info *o) {
+    if (!h || !o) return err(SLBM_EINVAL, "null argument");
+    const Domain &d = h->d;
+    o->n_voxels = d.n_vox;
+    o->n_fluid = d.n_fluid;
+    o->stride = d.S;
+    o->n_bc_links = d.n_links;
+    o->device_bytes = d.device_bytes;
+    o->step = d.step;
+    o->q = d.q;
+    o->op = d.op;
+    o->storage = d.storage;
+    o->layout = d.layout;
+    o->scale_exp = d.scale_exp;
+    o->pad = 0;
+    return ok();
+}
+
+slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_t *index_rows, int32_t *link_cell,
+                                    int32_t *link_dir, int32_t *link_type) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    const Domain &d = h->d;
+    if (d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "lists exist for the sparse layout only");
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const DevBuf &b, int64_t bytes) {
+        if (dst && bytes > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToHost, d.stream);
+    };
+    cp(cell_voxel, d.cell_voxel, d.n_fluid * 4);
+    cp(index_rows, d.P, (int64_t)(d.q - 1) * d.S * 4);
+    cp(link_cell, d.link_cell, d.n_links * 4);
+    cp(link_dir, d.link_dir, d.n_links * 4);
+    cp(link_type, d.link_type, d.n_links * 4);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    return e == cudaSuccess ? ok() : cuda_err(e, "export lists");
+}
+
+slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes) {
+    if (!h || !bytes) return err(SLBM_EINVAL, "null argument");
+    *bytes = (int64_t)h->d.q * h->d.S * h->d.bytes_per_pdf();
+    return ok();
+}
+
+slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step) {
+    if (!h || !host) return err(SLBM_EINVAL, "null argument");
+    const Domain &d = h->d;
+    const int64_t b = (int64_t)d.q * d.S * d.bytes_per_pdf();
+    cudaError_t e = cudaSuccess;
+    if (b) e = cudaMemcpyAsync(host, d.pdf.p, b, cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "get_state");
+    if (step) *step = d.step;
+    return ok();
+}
+
+slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step) {
+    if (!h || !host || step < 0) return err(SLBM_EINVAL, "bad argument");
+    Domain &d = h->d;
+    const int64_t b = (int64_t)d.q * d.S * d.bytes_per_pdf();
+    cudaError_t e = cudaSuccess;
+    if (b) e = cudaMemcpyAsync(d.pdf.p, host, b, cudaMemcpyHostToDevice, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "set_state");
+    d.step = step;
+    return ok();
+}
+
+slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells) {
+    if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
+    if (threads < 32 || threads > 256 || threads % 32) return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");
+    const bool okc = parity == 0 ? (cells == 1 || cells == 2 || cells == 4) : (cells == 1 || cells == 2);
+    if (!okc) return err(SLBM_EINVAL, "cells per thread: even 1/2/4, odd 1/2");
+    h->d.shape[parity] = LaunchShape{threads, cells};
+    drop_graphs(h->d);
+    return ok();
+}
+
+slbm_status sparse_lbm_set_checked(slbm_t *h, int32_t on) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    h->d.checked = on != 0;
+    drop_graphs(h->d);
+    return ok();
+}
+
+slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code) {
+    if (!h || !code) return err(SLBM_EINVAL, "null argument");
+    Domain &d = h->d;
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, d.err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err.p, 0, sizeof(int32_t), d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "device_error");
+    *code = v;
+    return v ? err(SLBM_EDEVICE, "a checked kernel latched an out-of-range slot") : ok();
+}
+
+void sparse_lbm_free(slbm_t *h) {
+    if (!h) return;
+    Domain &d = h->d;
+    cudaStreamSynchronize(d.stream);
+    drop_graphs(d);
+    release_all(d);
+    if (d.own_stream) cudaStreamDestroy(d.stream);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

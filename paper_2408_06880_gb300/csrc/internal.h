@@ -1,0 +1,105 @@
+// internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <utility>
+
+#include "common.cuh"
+#include "sparse_lbm.h"
+
+namespace slbm {
+
+// Thread-local error record behind sparse_lbm_last_error().
+void set_error(slbm_status s, const std::string &msg);
+slbm_status last_status();
+
+struct DevBuf {
+    void *p = nullptr;
+    int64_t bytes = 0;
+};
+
+// Allocation / error context of one API call on one domain.
+struct Ctx {
+    cudaStream_t stream = nullptr;
+    const slbm_allocator *hook = nullptr;
+    int64_t *held = nullptr;        // running total of bytes owned by the domain
+    slbm_status status = SLBM_OK;
+
+    int alloc(DevBuf &b, int64_t bytes);
+    void release(DevBuf &b);
+    int check(cudaError_t e, const char *what);
+    void fail(slbm_status s, const char *msg);
+};
+
+struct LaunchShape {
+    int32_t threads;
+    int32_t cells;
+};
+
+struct Domain {
+    // problem
+    int32_t nx = 0, ny = 0, nz = 0;
+    uint32_t periodic = 0;
+    int64_t n_vox = 0;
+    int32_t q = 19, op = SLBM_SRT, storage = SLBM_FP32, layout = SLBM_LAYOUT_SPARSE, scale_exp = 0;
+    double omega_p = 1.0, omega_m = 1.0, magic = 0.1875, force[3] = {0, 0, 0}, rho_out = 1.0;
+    // sizes
+    int64_t n_fluid = 0, S = 0, n_links = 0, step = 0;
+    // device data
+    DevBuf pdf;                        // Q x S stored populations
+    DevBuf P;                          // (Q-1) x S pull entries (sparse)
+    DevBuf cell_voxel;                 // N_F voxel ids (sparse)
+    DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
+    DevBuf mask;                       // per-voxel link mask (dense)
+    DevBuf red_partial;                // per-chunk FP64 partial sums
+    DevBuf red_out;                    // 5 doubles
+    DevBuf err;                        // latched device error word
+    // execution
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    slbm_allocator hook{};
+    bool has_hook = false;
+    int64_t device_bytes = 0;
+    LaunchShape shape[2] = {{256, 2}, {256, 1}};
+    bool checked = false;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, parity) -> exec
+
+    int bytes_per_pdf() const { return storage == SLBM_FP32 ? 4 : 2; }
+    int64_t red_chunks() const;
+    CollideParams collide_params() const;
+    Ctx ctx() {
+        Ctx c;
+        c.stream = stream;
+        c.hook = has_hook ? &hook : nullptr;
+        c.held = &device_bytes;
+        return c;
+    }
+};
+
+// Chunking of the deterministic reductions: fixed cells per chunk.
+constexpr int RED_THREADS = 256;
+constexpr int RED_CELLS_PER_THREAD = 8;
+constexpr int RED_CHUNK = RED_THREADS * RED_CELLS_PER_THREAD;
+
+// lists.cu
+int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
+                       int64_t n_inlet_u);
+// stream_collide.cu
+cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st);
+// macro.cu
+cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order, cudaStream_t st);
+cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st);
+cudaError_t launch_init_equilibrium(const Domain &d, const float *rho, const float *u, int order,
+                                    cudaStream_t st);
+// dense.cu
+int build_dense_mask(Ctx &cx, Domain &d, const uint8_t *d_flags);
+cudaError_t launch_dense_step(const Domain &d, int parity, cudaStream_t st);
+
+}  // namespace slbm
+
+struct slbm_domain {
+    slbm::Domain d;
+};

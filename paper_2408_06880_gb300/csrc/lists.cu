@@ -1,0 +1,350 @@
+// lists.cu -- device construction of the sparse data structure (Sec. 3.1):
+// compaction of fluid voxels into the PDF-list order, the pull index-list with
+// no-slip / periodic folded in (Sec. 3.1.1), and the inlet/outlet link table.
+//
+// The compaction is an exclusive prefix sum of (flag == fluid) over voxel ids,
+// so cell k is the k-th fluid voxel in ascending id: exactly the order of a
+// sequential scan, whatever the launch shape (integer sums are exact).
+#include "internal.h"
+
+namespace slbm {
+
+// ------------------------------------------------------------ block scan
+// Three-phase exclusive scan of an int-valued sequence produced by a functor:
+//   1. per-tile totals, 2. exclusive scan of the totals (one block),
+//   3. per-tile rescan that emits every element's exclusive prefix.
+// A tile is SCAN_THREADS x SCAN_ITEMS consecutive elements; thread t owns
+// elements [t*ITEMS, (t+1)*ITEMS) of its tile.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int32_t block_exclusive_sum(int32_t v, int32_t *smem_warp, int32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int32_t s = lane < nw ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) smem_warp[lane] = s;   // inclusive warp prefix
+    }
+    __syncthreads();
+    total = smem_warp[(blockDim.x >> 5) - 1];
+    const int32_t warp_base = warp > 0 ? smem_warp[warp - 1] : 0;
+    __syncthreads();
+    return warp_base + x - v;
+}
+
+template <class Fn>
+__global__ void scan_tile_totals(Fn fn, int64_t n, int32_t *tile_total) {
+    __shared__ int32_t sw[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) s += fn.value(base + j);
+    int32_t tot;
+    block_exclusive_sum(s, sw, tot);
+    if (threadIdx.x == 0) tile_total[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the tile totals in place; grand total out.
+__global__ void scan_tile_offsets(int32_t *tile_total, int64_t n_tiles, int32_t *grand) {
+    __shared__ int32_t sw[32];
+    int32_t carry = 0;
+    for (int64_t b = 0; b < n_tiles; b += blockDim.x) {
+        const int64_t i = b + threadIdx.x;
+        const int32_t v = i < n_tiles ? tile_total[i] : 0;
+        int32_t tot;
+        const int32_t ex = block_exclusive_sum(v, sw, tot);
+        if (i < n_tiles) tile_total[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+template <class Fn>
+__global__ void scan_tile_emit(Fn fn, int64_t n, const int32_t *tile_offset) {
+    __shared__ int32_t sw[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = base + j < n ? fn.value(base + j) : 0;
+        s += v[j];
+    }
+    int32_t tot;
+    int32_t run = tile_offset[blockIdx.x] + block_exclusive_sum(s, sw, tot);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) fn.emit(base + j, v[j], run);
+        run += v[j];
+    }
+}
+
+// Runs the scan; returns the grand total (synchronises `st`).
+template <class Fn>
+static int scan_run(Ctx &cx, Fn fn, int64_t n, int64_t *total) {
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 0) {
+        *total = 0;
+        return 0;
+    }
+    DevBuf tt, gr;
+    if (cx.alloc(tt, tiles * sizeof(int32_t)) || cx.alloc(gr, sizeof(int32_t))) return -1;
+    scan_tile_totals<<<(unsigned)tiles, SCAN_THREADS, 0, cx.stream>>>(fn, n, (int32_t *)tt.p);
+    scan_tile_offsets<<<1, 1024, 0, cx.stream>>>((int32_t *)tt.p, tiles, (int32_t *)gr.p);
+    scan_tile_emit<<<(unsigned)tiles, SCAN_THREADS, 0, cx.stream>>>(fn, n, (const int32_t *)tt.p);
+    int32_t h = 0;
+    if (cx.check(cudaMemcpyAsync(&h, gr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, cx.stream), "scan total") ||
+        cx.check(cudaStreamSynchronize(cx.stream), "scan sync"))
+        return -1;
+    cx.release(tt);
+    cx.release(gr);
+    *total = h;
+    return 0;
+}
+
+// ------------------------------------------------------------- functors
+struct FluidCompaction {           // cell order (Sec. 3.1)
+    const uint8_t *flags;
+    int32_t *cell_id, *cell_voxel;
+    __device__ int32_t value(int64_t v) const { return flags[v] == FLAG_FLUID; }
+    __device__ void emit(int64_t v, int32_t val, int32_t ex) const {
+        cell_id[v] = val ? ex : -1;
+        if (val) cell_voxel[ex] = (int32_t)v;
+    }
+};
+
+struct InletList {                 // ascending voxel ids of inlet voxels
+    const uint8_t *flags;
+    int32_t *inlet_voxel;
+    __device__ int32_t value(int64_t v) const { return flags[v] == FLAG_INLET; }
+    __device__ void emit(int64_t v, int32_t val, int32_t ex) const {
+        if (val) inlet_voxel[ex] = (int32_t)v;
+    }
+};
+
+struct CountScan {                 // exclusive offsets of per-cell link counts
+    const uint8_t *count;
+    int32_t *offset;
+    __device__ int32_t value(int64_t k) const { return count[k]; }
+    __device__ void emit(int64_t k, int32_t, int32_t ex) const { offset[k] = ex; }
+};
+
+// --------------------------------------------------------- neighbour walk
+struct Box {
+    int32_t nx, ny, nz;
+    uint32_t periodic;
+};
+
+// Voxel at x - c_i (the pull neighbour of direction i), or -1 when it lies
+// outside the box across a non-periodic face (treated as a wall).
+template <int Q>
+__device__ __forceinline__ int64_t pull_neighbour(const Box &b, int x, int y, int z, int i) {
+    int nx = x - cx(i), ny = y - cy(i), nz = z - cz(i);
+    if (nx < 0 || nx >= b.nx) {
+        if (!(b.periodic & 1u)) return -1;
+        nx = (nx + b.nx) % b.nx;
+    }
+    if (ny < 0 || ny >= b.ny) {
+        if (!(b.periodic & 2u)) return -1;
+        ny = (ny + b.ny) % b.ny;
+    }
+    if (nz < 0 || nz >= b.nz) {
+        if (!(b.periodic & 4u)) return -1;
+        nz = (nz + b.nz) % b.nz;
+    }
+    return (int64_t)nx + (int64_t)b.nx * ((int64_t)ny + (int64_t)b.ny * nz);
+}
+
+__device__ __forceinline__ void voxel_xyz(const Box &b, int64_t v, int &x, int &y, int &z) {
+    x = (int)(v % b.nx);
+    const int64_t r = v / b.nx;
+    y = (int)(r % b.ny);
+    z = (int)(r / b.ny);
+}
+
+template <int Q>
+__global__ void count_links(Box b, const uint8_t *flags, const int32_t *cell_voxel, int32_t nf,
+                            uint8_t *count) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    int x, y, z;
+    voxel_xyz(b, cell_voxel[k], x, y, z);
+    int c = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int64_t nb = pull_neighbour<Q>(b, x, y, z, i);
+        const uint8_t t = nb < 0 ? (uint8_t)FLAG_WALL : flags[nb];
+        c += (t == FLAG_INLET || t == FLAG_OUTLET);
+    }
+    count[k] = (uint8_t)c;
+}
+
+// Index of voxel v in the sorted inlet list (binary search), or -1.
+__device__ __forceinline__ int64_t inlet_rank(const int32_t *list, int64_t n, int64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (list[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && list[lo] == v) ? lo : -1;
+}
+
+// One thread per cell; writes its Q-1 pull entries (column k of each row) and
+// its boundary links.  Link maps are in shifted, unscaled units.
+template <int Q>
+__global__ void build_index(Box b, const uint8_t *flags, const int32_t *cell_id,
+                            const int32_t *cell_voxel, int32_t nf, int32_t S, int32_t *P,
+                            const int32_t *link_offset, int32_t *link_cell, int32_t *link_dir,
+                            int32_t *link_type, LinkMap *maps, const int32_t *inlet_voxel,
+                            int64_t n_inlet, const float *inlet_u, float rho_out) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S) return;
+    if (k >= nf) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) P[(int64_t)(i - 1) * S + k] = INT32_MIN;
+        return;
+    }
+    int x, y, z;
+    voxel_xyz(b, cell_voxel[k], x, y, z);
+    int32_t nb_link = link_offset ? link_offset[k] : 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int64_t nb = pull_neighbour<Q>(b, x, y, z, i);
+        const uint8_t t = nb < 0 ? (uint8_t)FLAG_WALL : flags[nb];
+        int32_t e;
+        if (t == FLAG_FLUID) {
+            e = i * S + cell_id[nb];
+        } else if (t == FLAG_WALL) {
+            e = inv(i) * S + k;
+        } else {
+            const int32_t l = nb_link++;
+            e = -(l + 1);
+            link_cell[l] = k;
+            link_dir[l] = i;
+            link_type[l] = t;
+            LinkMap m;
+            if (t == FLAG_INLET) {
+                float ux = 0.f, uy = 0.f, uz = 0.f;
+                if (inlet_u) {
+                    const int64_t r = inlet_rank(inlet_voxel, n_inlet, nb);
+                    if (r >= 0) {
+                        ux = inlet_u[3 * r];
+                        uy = inlet_u[3 * r + 1];
+                        uz = inlet_u[3 * r + 2];
+                    }
+                }
+                m.s = 1.0f;
+                m.a = 6.0f * wgt<Q>(i) * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+            } else {
+                m.s = -1.0f;
+                m.a = 2.0f * wgt<Q>(i) * (rho_out - 1.0f);
+            }
+            maps[l] = m;
+        }
+        P[(int64_t)(i - 1) * S + k] = e;
+    }
+}
+
+// ---------------------------------------------------------------- driver
+int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
+                       int64_t n_inlet_u) {
+    const int64_t N = d.n_vox;
+    Box b{d.nx, d.ny, d.nz, d.periodic};
+    DevBuf cell_id;
+    if (cx.alloc(cell_id, N * sizeof(int32_t)) || cx.alloc(d.cell_voxel, std::max<int64_t>(N, 1) * sizeof(int32_t)))
+        return -1;
+    int64_t nf = 0;
+    if (scan_run(cx, FluidCompaction{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p}, N, &nf)) return -1;
+    d.n_fluid = nf;
+    d.S = (nf + 127) / 128 * 128;
+    if ((int64_t)d.q * d.S >= ((int64_t)1 << 31)) {
+        cx.fail(SLBM_EUNSUPPORTED, "Q * stride >= 2^31: domain too large for int32 slots");
+        return -1;
+    }
+    // shrink cell_voxel to N_F entries
+    if (nf < N) {
+        DevBuf cv;
+        if (cx.alloc(cv, std::max<int64_t>(nf, 1) * sizeof(int32_t))) return -1;
+        if (nf && cx.check(cudaMemcpyAsync(cv.p, d.cell_voxel.p, nf * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                           cx.stream), "copy cell_voxel"))
+            return -1;
+        cx.release(d.cell_voxel);
+        d.cell_voxel = cv;
+        cv.p = nullptr;
+    }
+    if (d.S == 0) {
+        cx.release(cell_id);
+        return 0;
+    }
+    if (cx.alloc(d.P, (int64_t)(d.q - 1) * d.S * sizeof(int32_t))) return -1;
+
+    DevBuf link_count, link_offset, inlet_voxel, inlet_u;
+    int64_t n_links = 0, n_inlet = 0;
+    if (has_bc) {
+        if (cx.alloc(link_count, nf)) return -1;
+        const unsigned gb = (unsigned)((nf + 255) / 256);
+        if (d.q == 19)
+            count_links<19><<<gb, 256, 0, cx.stream>>>(b, d_flags, (int32_t *)d.cell_voxel.p, (int32_t)nf,
+                                                       (uint8_t *)link_count.p);
+        else
+            count_links<27><<<gb, 256, 0, cx.stream>>>(b, d_flags, (int32_t *)d.cell_voxel.p, (int32_t)nf,
+                                                       (uint8_t *)link_count.p);
+        if (cx.alloc(link_offset, nf * sizeof(int32_t))) return -1;
+        if (scan_run(cx, CountScan{(const uint8_t *)link_count.p, (int32_t *)link_offset.p}, nf, &n_links)) return -1;
+        cx.release(link_count);
+        d.n_links = n_links;
+        if (n_links) {
+            if (cx.alloc(d.link_cell, n_links * 4) || cx.alloc(d.link_dir, n_links * 4) ||
+                cx.alloc(d.link_type, n_links * 4) || cx.alloc(d.link_map, n_links * sizeof(LinkMap)))
+                return -1;
+        }
+        if (h_inlet_u) {
+            if (cx.alloc(inlet_voxel, std::max<int64_t>(n_inlet_u, 1) * sizeof(int32_t))) return -1;
+            if (scan_run(cx, InletList{d_flags, (int32_t *)inlet_voxel.p}, N, &n_inlet)) return -1;
+            if (n_inlet != n_inlet_u) {
+                cx.fail(SLBM_EINVAL, "n_inlet_u does not match the number of inlet voxels");
+                return -1;
+            }
+            if (cx.alloc(inlet_u, std::max<int64_t>(n_inlet, 1) * 3 * sizeof(float))) return -1;
+            if (n_inlet && cx.check(cudaMemcpyAsync(inlet_u.p, h_inlet_u, n_inlet * 3 * sizeof(float),
+                                                    cudaMemcpyHostToDevice, cx.stream), "inlet_u H2D"))
+                return -1;
+        }
+    }
+    const unsigned gs = (unsigned)((d.S + 255) / 256);
+    auto launch = [&](auto qtag) {
+        constexpr int QQ = decltype(qtag)::value;
+        build_index<QQ><<<gs, 256, 0, cx.stream>>>(
+            b, d_flags, (const int32_t *)cell_id.p, (const int32_t *)d.cell_voxel.p, (int32_t)nf, (int32_t)d.S,
+            (int32_t *)d.P.p, has_bc ? (const int32_t *)link_offset.p : nullptr, (int32_t *)d.link_cell.p,
+            (int32_t *)d.link_dir.p, (int32_t *)d.link_type.p, (LinkMap *)d.link_map.p,
+            (const int32_t *)inlet_voxel.p, n_inlet, (const float *)inlet_u.p, (float)d.rho_out);
+    };
+    if (d.q == 19) launch(std::integral_constant<int, 19>{});
+    else launch(std::integral_constant<int, 27>{});
+    if (cx.check(cudaGetLastError(), "build_index launch") || cx.check(cudaStreamSynchronize(cx.stream), "build sync"))
+        return -1;
+    cx.release(cell_id);
+    cx.release(link_offset);
+    cx.release(inlet_voxel);
+    cx.release(inlet_u);
+    return 0;
+}
+
+}  // namespace slbm

@@ -1,0 +1,252 @@
+"""GPU parity through the C ABI against the FP64 oracle.
+
+Bit-exact for the integer work (compaction order, pull index-list, link
+table); for FP32 storage the velocity relative L2 over all fluid cells and
+components must be <= 1e-5 (the stated tolerance), density within 1e-6."""
+import numpy as np
+import pytest
+
+import geometry as G
+import oracle as O
+from helpers import gpu_domain, gpu_fields, oracle_fields, oracle_problem, rel_l2, fluid_mask
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2408_06880_gb300")
+
+U_TOL = 1e-5
+RHO_TOL = 1e-6
+
+
+def _mixed_bc(seed=5, shape=(12, 9, 10)):
+    g = G.random_solids(shape, 0.25, seed, periodic=0b010)
+    f = g.flags
+    f[:, :, 0] = np.where(f[:, :, 0] == G.FLUID, G.INLET, f[:, :, 0])
+    f[:, :, -1] = np.where(f[:, :, -1] == G.FLUID, G.OUTLET, f[:, :, -1])
+    n_in = int(np.count_nonzero(f == G.INLET))
+    g.inlet_u = np.random.default_rng(seed).uniform(-0.02, 0.05, (n_in, 3))
+    g.rho_out = 1.001
+    return g
+
+
+LIST_CASES = {
+    "periodic8": lambda: G.random_solids(8, 0.3, 1, periodic=7),
+    "walled": lambda: G.random_solids((9, 7, 5), 0.3, 2, periodic=0),
+    "mixed_bc": _mixed_bc,
+    "spheres32": lambda: G.relaxed_spheres(),
+    "boolean64": lambda: G.boolean_spheres(64, 0.5, 3),
+    "all_fluid": lambda: G.Geometry(np.zeros((5, 6, 7), np.uint8), 7),
+}
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("case", list(LIST_CASES))
+def test_lists_bit_exact(q, case):
+    g = LIST_CASES[case]()
+    ref = O.pull_list(O.Problem.from_geometry(g, q=q))
+    with gpu_domain(g, q=q) as d:
+        got = d.export_lists()
+    assert got["n_fluid"] == ref.n_fluid and got["stride"] == ref.stride
+    assert np.array_equal(got["cell_voxel"], ref.cell_voxel)
+    assert np.array_equal(got["P"], ref.P)
+    assert np.array_equal(got["link_cell"], ref.bc_cell)
+    assert np.array_equal(got["link_dir"], ref.bc_dir)
+    assert np.array_equal(got["link_type"], ref.bc_type)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16, P.BF16])
+@pytest.mark.parametrize("op", [P.SRT, P.TRT])
+def test_rest_state_bitwise_zero(q, storage, op):
+    g = G.random_solids(12, 0.3, 4, periodic=0b011, walls_z=True)
+    with gpu_domain(g, q=q, storage=storage, op=op, scale_exp=10) as d:
+        d.step(11)
+        buf, step = d.get_state()
+        assert step == 11
+        assert not buf.any()
+        rho, u = gpu_fields(d)
+        m = fluid_mask(g)
+        assert np.all(rho[m] == 1.0) and not u.any()
+
+
+def test_small_case_parity_srt_d3q19():
+    # the 32^3 sphere packing, SRT tau = 0.8, F = 1e-6 x, 200 steps, FP32
+    g = G.relaxed_spheres()
+    kw = dict(q=19, op=P.SRT, omega=1.25, force=(1e-6, 0.0, 0.0))
+    (rho_o, u_o), _, _ = oracle_fields(g, 200, **kw)
+    with gpu_domain(g, **kw) as d:
+        d.step(200)
+        rho_g, u_g = gpu_fields(d)
+    m = fluid_mask(g)
+    assert rel_l2(u_g[m], u_o[m]) <= U_TOL
+    assert np.max(np.abs(rho_g[m] - rho_o[m])) <= RHO_TOL
+    assert np.max(np.abs(u_o[m])) > 1e-5
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("op", [P.SRT, P.TRT])
+def test_parity_forced_with_walls(q, op):
+    g = G.random_solids((24, 20, 18), 0.2, 7, periodic=0b011, walls_z=True)
+    kw = dict(q=q, op=op, omega=1.6, force=(2e-6, -1e-6, 5e-7))
+    (rho_o, u_o), _, _ = oracle_fields(g, 60, **kw)
+    with gpu_domain(g, **kw) as d:
+        d.step(60)
+        rho_g, u_g = gpu_fields(d)
+    m = fluid_mask(g)
+    assert rel_l2(u_g[m], u_o[m]) <= U_TOL
+    assert np.max(np.abs(rho_g[m] - rho_o[m])) <= RHO_TOL
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_parity_inlet_outlet_links(q):
+    g = _mixed_bc()
+    kw = dict(q=q, op=P.TRT, omega=1.25, force=(0.0, 0.0, 0.0))
+    (rho_o, u_o), _, _ = oracle_fields(g, 40, **kw)
+    with gpu_domain(g, **kw) as d:
+        assert d.info["n_bc_links"] > 0
+        d.step(40)
+        rho_g, u_g = gpu_fields(d)
+    m = fluid_mask(g)
+    assert rel_l2(u_g[m], u_o[m]) <= U_TOL
+    assert np.max(np.abs(rho_g[m] - rho_o[m])) <= RHO_TOL
+
+
+@pytest.mark.parametrize("steps", [1, 7, 33])
+def test_odd_parity_readout(steps):
+    # after an odd number of steps the state is read through the odd-step slots
+    g = _mixed_bc(9)
+    kw = dict(q=19, op=P.TRT, omega=1.4, force=(1e-5, 0.0, 0.0))
+    (rho_o, u_o), _, _ = oracle_fields(g, steps, **kw)
+    with gpu_domain(g, **kw) as d:
+        d.step(steps)
+        rho_g, u_g = gpu_fields(d)
+        s = d.reduce()
+    m = fluid_mask(g)
+    assert rel_l2(u_g[m], u_o[m]) <= U_TOL
+    assert np.max(np.abs(rho_g[m] - rho_o[m])) <= RHO_TOL
+    assert abs(s[4] - u_o[m, 0].sum()) <= 1e-5 * np.abs(u_o[m, 0]).sum() + 1e-12
+
+
+def test_taylor_green_initialisation_parity():
+    L, nz, U = 32, 4, 0.02
+    rho0, u0 = G.taylor_green_fields(L, nz, U)
+    g = G.Geometry(np.zeros((nz, L, L), np.uint8), 7)
+    kw = dict(q=19, op=P.SRT, omega=1.25)
+    (rho_o, u_o), _, _ = oracle_fields(g, 100, rho0, u0, **kw)
+    with gpu_domain(g, **kw) as d:
+        d.init_equilibrium(rho0, u0.T.copy(), order=P.ORDER_VOXELS)
+        d.step(100)
+        rho_g, u_g = gpu_fields(d)
+    assert rel_l2(u_g, u_o) <= U_TOL
+    assert np.max(np.abs(rho_g - rho_o)) <= RHO_TOL
+
+
+def test_reductions_match_fields_and_are_deterministic():
+    g = G.boolean_spheres(48, 0.5, 8)
+    kw = dict(q=19, op=P.TRT, force=(1e-5, 0.0, 0.0))
+    with gpu_domain(g, **kw) as d:
+        d.step(50)
+        s1, s2 = d.reduce(), d.reduce()
+        rho, u = d.macroscopic()
+    assert np.array_equal(s1, s2)
+    assert abs(s1[4] - np.sum(u[0].astype(np.float64))) <= 1e-6 * np.abs(u[0]).sum()
+    # momentum sum = sum rho u with the same fields
+    assert abs(s1[1] - np.sum(rho.astype(np.float64) * u[0])) <= 1e-5 * np.abs(rho * u[0]).sum()
+    # mass is conserved (periodic + bounce-back): sum(rho-1) stays at FP32 rounding level
+    assert abs(s1[0]) < 1e-6
+
+
+@pytest.mark.parametrize("shape", [(64, 1), (128, 1), (256, 1), (64, 2), (256, 2), (128, 4), (256, 4)])
+def test_launch_shapes_are_bitwise_identical(shape):
+    g = G.boolean_spheres(40, 0.5, 9)    # N_F not a multiple of any tile
+    kw = dict(q=19, op=P.TRT, force=(1e-5, 2e-6, 0.0))
+    with gpu_domain(g, **kw) as ref:
+        ref.step(6)
+        want, _ = ref.get_state()
+    threads, cells = shape
+    with gpu_domain(g, **kw) as d:
+        d.set_launch(0, threads, cells)
+        d.set_launch(1, threads, min(cells, 2))
+        d.step(6)
+        got, _ = d.get_state()
+    assert np.array_equal(got, want)
+
+
+def test_graph_replay_and_checked_mode_match_plain_steps():
+    g = _mixed_bc(11)
+    kw = dict(q=27, op=P.TRT, force=(1e-5, 0.0, 0.0))
+    with gpu_domain(g, **kw) as a:
+        a.step(10)
+        want, _ = a.get_state()
+    with gpu_domain(g, **kw) as b:
+        b.step(4, graph=True)
+        b.step(3, graph=True)
+        b.step(3, graph=True)
+        got, _ = b.get_state()
+    assert np.array_equal(got, want)
+    with gpu_domain(g, **kw) as c:
+        c.set_checked(True)
+        c.step(10)
+        assert c.device_error() == 0
+        got, _ = c.get_state()
+    assert np.array_equal(got, want)
+
+
+def test_checkpoint_resume_is_bitwise():
+    g = G.boolean_spheres(32, 0.6, 10)
+    kw = dict(q=19, op=P.TRT, force=(1e-5, 0.0, 0.0))
+    with gpu_domain(g, **kw) as a:
+        a.step(21)
+        want, _ = a.get_state()
+    with gpu_domain(g, **kw) as b:
+        b.step(13)
+        buf, step = b.get_state()
+    with gpu_domain(g, **kw) as c:
+        c.set_state(buf, step)
+        c.step(8)
+        got, s = c.get_state()
+    assert s == 21 and np.array_equal(got, want)
+
+
+def test_edge_cases_empty_and_single_cell():
+    solid = G.Geometry(np.ones((4, 4, 4), np.uint8), 7)
+    with gpu_domain(solid) as d:
+        assert d.n_fluid == 0
+        d.step(5)
+        assert np.array_equal(d.reduce(), np.zeros(5))
+    one = np.ones((3, 3, 3), np.uint8)
+    one[1, 1, 1] = 0
+    g = G.Geometry(one, 7)
+    kw = dict(q=19, op=P.SRT, force=(1e-4, 0, 0))
+    (rho_o, u_o), _, _ = oracle_fields(g, 9, **kw)
+    with gpu_domain(g, **kw) as d:
+        assert d.n_fluid == 1 and d.info["stride"] == 128
+        d.step(9)
+        rho_g, u_g = gpu_fields(d)
+    m = fluid_mask(g)
+    assert np.allclose(u_g[m], u_o[m], atol=1e-9, rtol=1e-5)
+
+
+def test_dense_comparator_parity():
+    g = G.random_solids((20, 16, 12), 0.3, 12, periodic=0b011, walls_z=True)
+    kw = dict(q=19, op=P.TRT, force=(1e-6, 0.0, 0.0))
+    (rho_o, u_o), _, _ = oracle_fields(g, 50, **kw)
+    with gpu_domain(g, layout=P.DENSE, **kw) as d:
+        d.step(50)
+        rho_g, u_g = gpu_fields(d)
+        s = d.reduce()
+    m = fluid_mask(g)
+    assert rel_l2(u_g[m], u_o[m]) <= U_TOL
+    assert np.max(np.abs(rho_g[m] - rho_o[m])) <= RHO_TOL
+    assert abs(s[4] - u_o[m, 0].sum()) <= 1e-5 * np.abs(u_o[m, 0]).sum()
+
+
+def test_invalid_calls_report_status():
+    g = G.random_solids(8, 0.3, 1)
+    with gpu_domain(g) as d:
+        with pytest.raises(P.SlbmError):
+            d.set_launch(0, 100, 1)
+        with pytest.raises(P.SlbmError):
+            d.set_launch(1, 128, 4)
+        with pytest.raises(P.SlbmError):
+            d.step(-1)
