@@ -22,7 +22,11 @@ LIB = os.path.join(LIBDIR, "libsparse_lbm.so")
 
 SOURCES = ["api.cu", "lists.cu", "aa_q19.cu", "aa_q27.cu", "macro.cu", "dense.cu", "pool.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# -fmad=false: every multiply and add is rounded separately, in program order,
+# so all kernel instantiations (launch shapes, batched or not) produce the same
+# bits for the same cell.  The kernels are memory-bound; the unfused FP work
+# does not show.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 
