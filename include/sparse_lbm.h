@@ -176,6 +176,42 @@ slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code);
 /* Release everything; NULL is a no-op. */
 void sparse_lbm_free(slbm_t *h);
 
+/* Largest voxel count sparse_lbm_compact_noalloc accepts (65536 scan tiles of
+ * 4096 voxels; e.g. a 1024 x 512 x 512 box). */
+#define SLBM_NOALLOC_MAX_VOXELS 268435456
+
+/* Fluid-cell compaction that allocates nothing (the paper has no counterpart;
+ * it is a service for callers that cannot let a library allocate).
+ *
+ * Who needs it: callers that own every byte of device memory themselves -- a
+ * framework that reserves one arena up front and forbids other allocations,
+ * or a latency-critical loop where cudaMalloc/cudaFree, which may synchronise
+ * the whole device, are not acceptable.  They pass device buffers in and get
+ * results out; the call makes no cudaMalloc, cudaFree or other allocating
+ * library call.
+ *
+ * What it computes: the same compaction sparse_lbm_create uses (Sec. 3.1):
+ * cell_id[v] = rank of voxel v among fluid voxels (flag 0) in ascending voxel
+ * id, or -1; cell_voxel[k] = voxel id of fluid cell k; *n_fluid = count.
+ * All pointers are DEVICE pointers: flags[n_voxels] (uint8), cell_id[n_voxels],
+ * cell_voxel[capacity >= number of fluid voxels], n_fluid[1] (int32).  The work
+ * is enqueued on `stream` (cudaStream_t or NULL) and the call returns without
+ * waiting; read *n_fluid after synchronising the stream.
+ *
+ * Scratch: the scan's per-tile totals live in one fixed device array inside
+ * the library (256 KiB), which every GPU that loads the library holds until
+ * the process exits.  All calls share it and it keeps the last call's
+ * contents; each call overwrites what it reads first.  Calls that overlap on
+ * the GPU (e.g. on two streams at once) race on it: serialise them.  The first
+ * call on each device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ *
+ * Errors: SLBM_EINVAL if n_voxels < 0, n_voxels > SLBM_NOALLOC_MAX_VOXELS or a
+ * needed pointer is NULL (nothing is launched); SLBM_ECUDA if the device or a
+ * launch fails. */
+slbm_status sparse_lbm_compact_noalloc(const uint8_t *flags, int64_t n_voxels, int32_t *cell_id,
+                                       int32_t *cell_voxel, int32_t *n_fluid, void *stream);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *sparse_lbm_last_error(void);
 

@@ -16,6 +16,7 @@ FP32, FP16, BF16 = 0, 1, 2
 SPARSE, DENSE = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 ORDER_CELLS, ORDER_VOXELS = 0, 1
+NOALLOC_MAX_VOXELS = 268435456
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "EDIVERGED",
                 6: "ETIMEOUT", 7: "EABORTED", 8: "EDEVICE"}
 
@@ -69,6 +70,7 @@ SIGNATURES = {
     "sparse_lbm_device_error": (_st, [_vp, C.POINTER(_i32)]),
     "sparse_lbm_free": (None, [_vp]),
     "sparse_lbm_last_error": (C.c_char_p, []),
+    "sparse_lbm_compact_noalloc": (_st, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "slbm_pool_create": (_st, [_i32, _i32, _i32, _vp, C.POINTER(_vp)]),
     "slbm_pool_add": (_st, [_vp, _vp, C.POINTER(_i32)]),
     "slbm_pool_remove": (_st, [_vp, _i32]),

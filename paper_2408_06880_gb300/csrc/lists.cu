@@ -348,3 +348,83 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
 }
 
 }  // namespace slbm
+
+// ------------------------------------------------ allocation-free compaction
+// sparse_lbm_compact_noalloc: the same three-phase compaction scan, with the
+// per-tile totals kept in a fixed device array that lives as long as the
+// library stays loaded, instead of in memory allocated per call.
+#include <mutex>
+
+namespace slbm {
+
+constexpr int64_t NOALLOC_MAX_TILES = 65536;   // SLBM_NOALLOC_MAX_VOXELS / SCAN_TILE
+static_assert(NOALLOC_MAX_TILES * SCAN_TILE == SLBM_NOALLOC_MAX_VOXELS, "limit mismatch");
+
+// Tile totals of the scan (256 KiB).  Every call overwrites the entries it
+// uses before reading them, so nothing needs clearing between calls.
+static __device__ __align__(256) int32_t g_noalloc_tiles[NOALLOC_MAX_TILES];
+
+// Device address of g_noalloc_tiles per device, looked up once per device
+// (the host-side name of the array is not a device address).
+static std::mutex g_noalloc_mu;
+static int32_t *g_noalloc_addr[128] = {};
+
+static int noalloc_scratch(int32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 128) {
+        cudaGetLastError();
+        set_error(SLBM_ECUDA, "sparse_lbm_compact_noalloc: no current CUDA device");
+        return -1;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error(SLBM_ECUDA, std::string("sparse_lbm_compact_noalloc: cudaGetSymbolAddress: ") +
+                                      cudaGetErrorString(e));
+            return -1;
+        }
+        g_noalloc_addr[dev] = (int32_t *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return 0;
+}
+
+}  // namespace slbm
+
+extern "C" slbm_status sparse_lbm_compact_noalloc(const uint8_t *flags, int64_t n_voxels, int32_t *cell_id,
+                                                  int32_t *cell_voxel, int32_t *n_fluid, void *stream) {
+    using namespace slbm;
+    if (n_voxels < 0 || n_voxels > SLBM_NOALLOC_MAX_VOXELS) {
+        set_error(SLBM_EINVAL, "sparse_lbm_compact_noalloc: n_voxels must lie in [0, SLBM_NOALLOC_MAX_VOXELS = "
+                               "268435456]");
+        return SLBM_EINVAL;
+    }
+    if (!n_fluid || (n_voxels > 0 && (!flags || !cell_id || !cell_voxel))) {
+        set_error(SLBM_EINVAL, "sparse_lbm_compact_noalloc: null device pointer");
+        return SLBM_EINVAL;
+    }
+    int32_t *tiles = nullptr;
+    if (noalloc_scratch(&tiles)) return SLBM_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (n_voxels == 0) {
+        e = cudaMemsetAsync(n_fluid, 0, sizeof(int32_t), st);
+    } else {
+        const int64_t nt = (n_voxels + SCAN_TILE - 1) / SCAN_TILE;
+        const FluidCompaction fn{flags, cell_id, cell_voxel};
+        scan_tile_totals<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(fn, n_voxels, tiles);
+        scan_tile_offsets<<<1, 1024, 0, st>>>(tiles, nt, n_fluid);
+        scan_tile_emit<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(fn, n_voxels, tiles);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error(SLBM_ECUDA, std::string("sparse_lbm_compact_noalloc: ") + cudaGetErrorString(e));
+        return SLBM_ECUDA;
+    }
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
