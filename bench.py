@@ -60,6 +60,20 @@ def parse():
     ap.add_argument("--size", type=int, default=N)
     ap.add_argument("--no-extras", action="store_true", help="skip dense / FP16 / e2e / CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="PDF storage of the timed domains (the headline metric is FP32)")
+    ap.add_argument("--shape-even", default=None, help="threads,cells,variant of the even kernel")
+    ap.add_argument("--shape-odd", default=None, help="threads,cells,variant of the odd kernel")
+    ap.add_argument("--mode", default="kernel", choices=["kernel", "serve"],
+                    help="kernel: the porosity sweep (default); serve: the permeability-request stream")
+    ap.add_argument("--requests", type=int, default=64, help="serve mode: number of requests")
+    ap.add_argument("--max-steps", type=int, default=20000, help="serve mode: step cap per request")
+    ap.add_argument("--budget-gb", type=float, default=16.0, help="serve mode: HBM admission budget")
+    ap.add_argument("--capacity", type=int, default=128, help="serve mode: pool slots")
+    ap.add_argument("--arrivals", default="closed", choices=["closed", "poisson"],
+                    help="serve mode: all at t=0, or Poisson arrivals at --load x the measured capacity")
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--sequential", action="store_true", help="serve mode: also time one-at-a-time solves")
     a = ap.parse_args()
     if a.lbm_steps % 2:
         raise SystemExit("--lbm-steps must be even (whole AA pairs)")
@@ -135,10 +149,13 @@ def run_ours(a, rank, world):
     stream = torch.cuda.Stream()
     peak, peak_kind = load_peaks()
     doms = []
+    storage = {"fp32": P.FP32, "fp16": P.FP16, "bf16": P.BF16}[a.storage]
+    b_pdf = 4 if storage == P.FP32 else 2
     for phi in a.porosities:
         g = geometry_for(phi, a.size)
         d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
-                     stream=stream)
+                     storage=storage, scale_exp=P.auto_scale_exp(1e-3), stream=stream)
+        apply_shapes(d, a)
         doms.append((phi, g, d))
     half = a.lbm_steps // 2
 
@@ -191,7 +208,7 @@ def run_ours(a, rank, world):
         ev_ms = [e[0].elapsed_time(e[1]) for e in events[j]]
         od_ms = [e[1].elapsed_time(e[2]) for e in events[j]]
         nf = d.n_fluid
-        be, bo = algorithmic_bytes(nf, 4, parity=0), algorithmic_bytes(nf, 4, parity=1)
+        be, bo = algorithmic_bytes(nf, b_pdf, parity=0), algorithmic_bytes(nf, b_pdf, parity=1)
         me, mo = float(np.mean(ev_ms)), float(np.mean(od_ms))
         tot[0][0] += be * len(ev_ms)
         tot[0][1] += sum(ev_ms)
@@ -215,12 +232,15 @@ def run_ours(a, rank, world):
                 "both_kernels": {"even_gbs": round(tot[0][0] / tot[0][1] / 1e6, 1),
                                  "odd_gbs": round(tot[1][0] / tot[1][1] / 1e6, 1),
                                  "even_share": round(tot[0][1] / (tot[0][1] + tot[1][1]), 3)}}
-    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+    metric = METRIC if a.storage == "fp32" else METRIC.replace("FP32", a.storage.upper() + " storage")
+    out = {"metric": metric, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": round(elapsed_ms / a.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16 storage, f32 math",
+                                                          "bf16": "bf16 storage, f32 math"}[a.storage],
+           "data": "synthetic",
            "config": {"workload": f"{a.size}^3 periodic Boolean sphere packings, porosity "
                                   f"{'/'.join(str(p) for p in a.porosities)}, D3Q19 TRT magic 3/16, tau 0.8, "
-                                  f"F=1e-6 x, FP32 PDFs",
+                                  f"F=1e-6 x, {a.storage.upper()} PDFs",
                       "lbm_steps_per_step": a.lbm_steps, "domains": len(doms),
                       "l2": "inputs larger than L2 (PDF-list >= 0.38 GB per domain), no flush",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -234,6 +254,13 @@ def run_ours(a, rank, world):
     for _, _, d in doms:
         d.close()
     return out
+
+
+def apply_shapes(d, a):
+    for parity, spec in ((0, a.shape_even), (1, a.shape_odd)):
+        if spec:
+            t, c, v = (int(x) for x in spec.split(","))
+            d.set_launch(parity, t, c, v)
 
 
 def traffic_for(kname, doms):
@@ -376,8 +403,69 @@ def run_reference(a):
             "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def serve_requests(n, max_steps):
+    """The permeability-request stream: request i is a periodic Boolean sphere
+    packing of edge in {64, 96, 128, 192}, porosity U(0.3, 0.8), radii
+    U(6, 12), seed 41000 + i, D3Q19 TRT body-forced (F = 1e-6 x)."""
+    import geometry as G
+    from paper_2408_06880_gb300.serving import Request
+    reqs = []
+    for i in range(n):
+        g = G.serving_request(i)
+        reqs.append(Request(i, g.flags, force=FORCE, omega=OMEGA, trt_magic=MAGIC, max_steps=max_steps, tol=1e-6,
+                            meta=dict(edge=g.meta["edge"], porosity=g.porosity)))
+    return reqs
+
+
+def run_serve(a):
+    """Serve mode: continuous batching of the request stream (closed batch or
+    Poisson arrivals), optionally against one-at-a-time solves."""
+    import torch
+    import paper_2408_06880_gb300 as P
+    from paper_2408_06880_gb300.serving import GpuExecutor, Server, solve_alone
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    storage = {"fp32": P.FP32, "fp16": P.FP16, "bf16": P.BF16}[a.storage]
+    reqs = serve_requests(a.requests, a.max_steps)
+    out = {"metric": "solves/s (continuous batching, permeability requests)", "unit": "solves/s",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "storage": a.storage,
+           "config": {"workload": f"{a.requests} permeability requests: periodic Boolean packings, edge "
+                                  f"{{64,96,128,192}}, porosity U(0.3,0.8), D3Q19 TRT F=1e-6, converge to "
+                                  f"1e-6 relative change of mean u_x per 100 steps or {a.max_steps} steps",
+                      "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals}}
+    ex = GpuExecutor(Q, storage, capacity=a.capacity)
+    srv = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    clocks.start()
+    res, st = srv.run(reqs, realtime=False)
+    out["clocks"] = clocks.stop()
+    out["closed_batch"] = st
+    out["value"] = round(st["solves_per_s"], 4)
+    if a.arrivals == "poisson":
+        rate = a.load * st["solves_per_s"]
+        rng = np.random.default_rng(4100)
+        t = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        for r, ti in zip(reqs, t):
+            r.arrival = float(ti)
+        res_p, st_p = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100).run(reqs, realtime=True)
+        out["poisson"] = dict(st_p, rate_per_s=rate)
+    ex.close()
+    out["results"] = [{"rid": r.rid, "k": r.permeability, "steps": r.steps, "converged": r.converged,
+                       "latency_s": round(r.latency, 4), "error": r.error} for r in sorted(res, key=lambda r: r.rid)]
+    if a.sequential:
+        t0 = time.perf_counter()
+        alone = [solve_alone(r, storage=storage) for r in reqs]
+        wall = time.perf_counter() - t0
+        out["one_at_a_time"] = {"solves_per_s": len(alone) / wall, "wall_s": wall}
+        k_alone = {r.rid: r.permeability for r in alone}
+        out["served_equals_alone"] = all(r.permeability == k_alone[r.rid] for r in res if r.error is None)
+    return out
+
+
 def main():
     a = parse()
+    if a.mode == "serve" and a.impl == "ours":
+        print(json.dumps(run_serve(a)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if a.impl == "reference":

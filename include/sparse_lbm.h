@@ -149,8 +149,12 @@ slbm_status sparse_lbm_init_equilibrium(slbm_t *h, const float *rho, const float
 slbm_status sparse_lbm_info(const slbm_t *h, slbm_info *out);
 
 /* Copy the sparse lists to HOST buffers (any pointer may be NULL):
- * cell_voxel[N_F]; index_rows[(Q-1)*S] (row r = direction r+1); link_cell,
- * link_dir, link_type [n_bc_links]. Synchronous. Sparse layout only. */
+ * cell_voxel[N_F]; index_rows[(Q-1)*S] = the canonical pull entries P(i,k)
+ * (row r = direction r+1, values as in sparse_lbm_create); link_cell,
+ * link_dir, link_type [n_bc_links]. Synchronous. Sparse layout only.
+ * (On the device the list is kept with each non-negative entry's row flipped
+ * between i and inverse(i) -- the slot the AA odd step reads; the export
+ * flips it back, exactly.) */
 slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_t *index_rows,
                                     int32_t *link_cell, int32_t *link_dir, int32_t *link_type);
 
@@ -161,10 +165,16 @@ slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes);
 slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step);
 slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
 
-/* Launch shape used for a parity (0 even, 1 odd): threads per block (multiple
- * of 32, <= 1024) and cells per thread (1, 2 or 4; odd step: 1 or 2).
- * Chosen by the autotuner; defaults are 256 x 2 (even) and 256 x 1 (odd). */
-slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells);
+/* Launch shape used for a parity (0 even, 1 odd), chosen by the autotuner.
+ * variant 0: one thread per `cells` consecutive cells (even 1/2/4, odd 1/2),
+ *            `threads` per block (32..256, multiple of 32);
+ * variant 1: persistent CTAs (SMs x resident CTAs) that walk tiles of
+ *            `threads` cells (64 or 128) and keep `cells` tiles (2 or 4) of
+ *            index-list rows (odd) or PDF rows (even) in flight in shared
+ *            memory through asynchronous bulk copies; sparse FP32/FP16 only.
+ * Defaults: variant 0, 64 x 2 (even; FP16: variant 1, 128 x 2) and 64 x 1
+ * (odd).  Results are bit-for-bit the same for every shape. */
+slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch
  * SLBM_EDEVICE instead of touching memory out of range; 0 = fast path. */
@@ -218,21 +228,40 @@ const char *sparse_lbm_last_error(void);
 /* ---- batching: many domains stepped by one persistent kernel ----------------
  * A pool steps every member domain through one launch per time step: the
  * members' compacted cell lists are concatenated through a device domain table
- * (per-domain cell offset, stride, parity, rates, force, link table), so small
- * domains share the GPU.  Members keep their own memory and handles; all must
- * share q and storage.  Reductions are per member and bit-identical to
- * sparse_lbm_reduce on the same state. */
+ * (per-domain tile offset, stride, parity, rates, force, link maps) that a
+ * persistent grid walks tile by tile, so many small domains share the GPU in
+ * one launch, each at its own AA parity (Sec. 5.1).  Members keep their own
+ * memory and handles; all must share q and storage.  The per-cell arithmetic
+ * is the single-domain kernels', so a member's state evolves bit for bit as it
+ * would alone.  Pool work runs on the pool's stream: synchronise it (any pool
+ * call that returns host data does) before using a member handle directly. */
 slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream,
                              slbm_pool_t **out);
+/* Add a domain (not owned by the pool) to a free slot; SLBM_ENOMEM if full. */
 slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot);
+/* Remove a member after its queued pool work has finished (synchronises). */
 slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot);
 /* k >= 0 steps on every member (each at its own parity); use_graph != 0
- * replays a captured CUDA graph of the k launches. */
+ * replays a CUDA graph of the k launches, captured once per k and kept valid
+ * across membership changes (the table is rewritten instead). */
 slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph);
-/* out: 5 doubles per slot (capacity x 5), device or host; unused slots zero. */
+/* out: 5 doubles per slot (capacity x 5, layout as sparse_lbm_reduce), device
+ * or host; free slots are zero.  Bit-identical to sparse_lbm_reduce of each
+ * member.  Host mode returns SLBM_EABORTED if an abort was raised since the
+ * last clear. */
 slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem);
-/* Persistent-kernel shape (threads per block, CTAs per SM; 0 = auto). */
+/* Launch variant.  ctas_per_sm == 0 (default): tile grid -- one CTA of 128
+ * threads per tile of the concatenated cell lists (256-cell tiles for the even
+ * step, 128-cell tiles for the odd step), from per-tile descriptors built on
+ * the device when the membership changes (threads is ignored).  ctas_per_sm > 0: persistent walker
+ * with `threads` cells per tile (32..128, multiple of 32) and at most
+ * ctas_per_sm CTAs per SM. */
 slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm);
+/* raise != 0: set the host-mapped abort word; running and queued pool launches
+ * stop at their next tile and the members' states are left part-way through
+ * a step (restore them from a checkpoint).  raise == 0: wait for the pool's
+ * stream, then clear the word and the latched status. */
+slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise);
 void slbm_pool_free(slbm_pool_t *p);
 
 #ifdef __cplusplus

@@ -8,6 +8,7 @@ hand-written CUDA for sm_103a behind the C ABI of include/sparse_lbm.h.
 from ._capi import (BF16, DENSE, FP16, FP32, MEM_DEVICE, MEM_HOST, ORDER_CELLS, ORDER_VOXELS,
                     SPARSE, SRT, TRT, SlbmError, lib)
 from .domain import Domain, TorchAllocator, auto_scale_exp
+from .pool import Pool
 
-__all__ = ["Domain", "TorchAllocator", "auto_scale_exp", "SlbmError", "lib", "SRT", "TRT", "FP32", "FP16",
+__all__ = ["Domain", "Pool", "TorchAllocator", "auto_scale_exp", "SlbmError", "lib", "SRT", "TRT", "FP32", "FP16",
            "BF16", "SPARSE", "DENSE", "MEM_DEVICE", "MEM_HOST", "ORDER_CELLS", "ORDER_VOXELS"]

@@ -65,7 +65,7 @@ SIGNATURES = {
     "sparse_lbm_state_bytes": (_st, [_vp, C.POINTER(_i64)]),
     "sparse_lbm_get_state": (_st, [_vp, _vp, C.POINTER(_i64)]),
     "sparse_lbm_set_state": (_st, [_vp, _vp, _i64]),
-    "sparse_lbm_set_launch": (_st, [_vp, _i32, _i32, _i32]),
+    "sparse_lbm_set_launch": (_st, [_vp, _i32, _i32, _i32, _i32]),
     "sparse_lbm_set_checked": (_st, [_vp, _i32]),
     "sparse_lbm_device_error": (_st, [_vp, C.POINTER(_i32)]),
     "sparse_lbm_free": (None, [_vp]),
@@ -77,6 +77,7 @@ SIGNATURES = {
     "slbm_pool_step": (_st, [_vp, _i32, _i32]),
     "slbm_pool_reduce": (_st, [_vp, _vp, _i32]),
     "slbm_pool_set_launch": (_st, [_vp, _i32, _i32]),
+    "slbm_pool_abort": (_st, [_vp, _i32]),
     "slbm_pool_free": (None, [_vp]),
 }
 

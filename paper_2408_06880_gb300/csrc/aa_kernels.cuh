@@ -8,8 +8,9 @@
 //     inverse(i) of column k.
 //   odd step (t odd): f_i(x_k) is the post-collision value of direction i of
 //     the pull neighbour x_k - c_i, which the even step left in row inverse(i)
-//     of that neighbour's column; flipping the row of the pull entry gives its
-//     slot R(i,k).  Read all R(i,k), collide, and write the post-collision
+//     of that neighbour's column: the slot R(i,k), which is the pull entry
+//     P(i,k) with its row flipped between i and inverse(i).  The device
+//     index-list stores R(i,k) directly (see lists.cu).  Read all R(i,k), collide, and write the post-collision
 //     value of direction inverse(i) back into R(i,k).  R(i,k) lies in row
 //     inverse(i) of the neighbour x_k - c_i, which is the natural slot of
 //     f_inverse(i) at that neighbour for the next time level (or, at a wall,
@@ -75,16 +76,16 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
     for (int i = 0; i < Q; ++i) {
         const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + i * S + k0);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) g[c][i] = St::ld(x.v[c], p.inv_scale);
+        for (int c = 0; c < CPT; ++c) g[c][i] = St::raw(x.v[c]);
     }
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) collide<Q>(g[c], p);
+    for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
     const bool full = k0 + CPT <= nf;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         Vec<T, CPT> y;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) y.v[c] = St::st(g[c][i], p.scale);
+        for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(g[c][i]);
         T *dst = pdf + inv(i) * S + k0;
         if (full) {
             st_vec<T, CPT>(dst, y);
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
     {
         const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + k0);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) g[c][0] = St::ld(x.v[c], p.inv_scale);
+        for (int c = 0; c < CPT; ++c) g[c][0] = St::raw(x.v[c]);
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
@@ -130,10 +131,9 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             int32_t ee = e[c][i];
-            int32_t r = ee >= 0 ? flip_row(ee, i, S) : i * S + k;
+            int32_t r = ee >= 0 ? ee : i * S + k;
             if (CHECK) {
-                const bool bad = ee >= 0 ? (ee >= Q * S || r < 0 || r >= Q * S || r % S >= nf)
-                                         : (-(ee + 1) >= n_links);
+                const bool bad = ee >= 0 ? (ee >= Q * S || r % S >= nf) : (-(ee + 1) >= n_links);
                 if (bad) {
                     latch(err, 1 + i);
                     r = i * S + k;
@@ -141,20 +141,20 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
                 }
             }
             R[c][i] = r;
-            if (valid) g[c][i] = St::ld(pdf[r], p.inv_scale);
+            if (valid) g[c][i] = St::raw(pdf[r]);
             else g[c][i] = 0.f;
             if (HAS_BC && valid && ee < 0) {
                 const LinkMap m = maps[-(ee + 1)];
-                g[c][i] = m.s * g[c][i] + m.a;
+                g[c][i] = m.s * g[c][i] + m.a * p.scale;
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) collide<Q>(g[c], p);
+    for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
     {
         Vec<T, CPT> y;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) y.v[c] = St::st(g[c][0], p.scale);
+        for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(g[c][0]);
         if (k0 + CPT <= nf) {
             st_vec<T, CPT>(pdf + k0, y);
         } else {
@@ -171,11 +171,194 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
             float v = g[c][inv(i)];
             if (HAS_BC && e[c][i] < 0) {
                 const LinkMap m = maps[-(e[c][i] + 1)];
-                v = m.s * v + m.a;
+                v = m.s * v + m.a * p.scale;
             }
-            pdf[R[c][i]] = St::st(v, p.scale);
+            pdf[R[c][i]] = St::pack(v);
         }
     }
+}
+
+}  // namespace slbm
+
+// ---------------------------------------------------------------------------
+// Persistent variants with asynchronous bulk staging (Blackwell bulk-copy
+// engine, cp.async.bulk + mbarrier transaction counts).  Each CTA walks tiles
+// of TILE cells (tile, tile + gridDim, ...).  One elected thread keeps NSTAGE
+// tiles in flight: for the odd step the Q-1 index-list rows of the tile, for
+// the even step the Q PDF rows.  Threads read their column from shared
+// memory, so the index (or PDF) round trip of the next tiles overlaps the
+// gathers, collision and stores of the current one.  Waits are bounded; a
+// timeout latches an error code in *err and every thread of the CTA leaves
+// the loop together, after the elected thread has waited (bounded) for the
+// copies it still has in flight.  TILE divides 128 and the row stride S is a
+// multiple of 128, so every tile is whole and every copy is 16-byte aligned.
+#include "bulk.cuh"
+
+namespace slbm {
+
+constexpr int32_t ERR_STAGE_TIMEOUT = 100;
+
+// The odd-step update of one cell from its Q-1 pull entries.
+template <int Q, int ST, bool HAS_BC>
+__device__ __forceinline__ void odd_cell(typename Store<ST>::T *__restrict__ pdf, const int32_t (&e)[Q],
+                                         int32_t k, int32_t S, const LinkMap *__restrict__ maps,
+                                         const CollideParams &p) {
+    using St = Store<ST>;
+    int32_t R[Q];
+    float g[Q];
+    g[0] = St::raw(pdf[k]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int32_t ee = e[i];
+        R[i] = (HAS_BC && ee < 0) ? i * S + k : ee;
+        g[i] = St::raw(pdf[R[i]]);
+        if (HAS_BC && ee < 0) {
+            const LinkMap m = maps[-(ee + 1)];
+            g[i] = m.s * g[i] + m.a * p.scale;
+        }
+    }
+    collide<Q, St::scaled>(g, p);
+    pdf[k] = St::pack(g[0]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        float v = g[inv(i)];
+        if (HAS_BC && e[i] < 0) {
+            const LinkMap m = maps[-(e[i] + 1)];
+            v = m.s * v + m.a * p.scale;
+        }
+        pdf[R[i]] = St::pack(v);
+    }
+}
+
+// Pipeline bookkeeping kept by the elected thread: which stages have a copy
+// in flight and the parity of each stage's next completion.
+struct StageState {
+    uint32_t pending = 0, phase = 0;
+};
+
+template <int NSTAGE>
+__device__ __forceinline__ void drain_stages(uint64_t *bar, const StageState &ss) {
+#pragma unroll
+    for (int s = 0; s < NSTAGE; ++s)
+        if (ss.pending >> s & 1u) mbar_wait_bounded(&bar[s], ss.phase >> s & 1u);
+}
+
+template <int Q, int ST, bool HAS_BC, int TILE, int NSTAGE>
+__global__ void __launch_bounds__(TILE) aa_odd_staged_kernel(typename Store<ST>::T *__restrict__ pdf,
+                                                             const int32_t *__restrict__ P, int32_t S,
+                                                             int32_t nf, const LinkMap *__restrict__ maps,
+                                                             CollideParams p, int32_t *err) {
+    constexpr int R1 = Q - 1;
+    __shared__ __align__(128) int32_t tile[NSTAGE][R1][TILE];
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    const int tid = threadIdx.x;
+    const int32_t n_tiles = S / TILE;
+    StageState ss;
+    auto issue = [&](int32_t t, int s) {
+        mbar_arrive_expect_tx(&bar[s], R1 * TILE * 4);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) bulk_g2s(&tile[s][r][0], P + r * S + t * TILE, TILE * 4, &bar[s]);
+        ss.pending |= 1u << s;
+    };
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NSTAGE; ++s) {
+            const int32_t t = blockIdx.x + s * gridDim.x;
+            if (t < n_tiles) issue(t, s);
+        }
+    }
+    int it = 0;
+    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+        const int s = it % NSTAGE;
+        const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+        const bool ok = mbar_wait_bounded(&bar[s], ph);
+        int32_t e[Q];
+        e[0] = 0;
+        if (ok) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) e[r + 1] = tile[s][r][tid];
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) latch(err, ERR_STAGE_TIMEOUT);
+            break;
+        }
+        if (tid == 0) {
+            ss.pending &= ~(1u << s);
+            ss.phase ^= 1u << s;
+            const int32_t tn = t + NSTAGE * gridDim.x;
+            if (tn < n_tiles) issue(tn, s);
+        }
+        const int32_t k = t * TILE + tid;
+        if (k < nf) odd_cell<Q, ST, HAS_BC>(pdf, e, k, S, maps, p);
+    }
+    if (tid == 0 && ss.pending) drain_stages<NSTAGE>(bar, ss);
+    __syncthreads();
+}
+
+template <int Q, int ST, int TILE, int NSTAGE>
+__global__ void __launch_bounds__(TILE) aa_even_staged_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
+                                                              int32_t nf, CollideParams p, int32_t *err) {
+    using St = Store<ST>;
+    using T = typename St::T;
+    __shared__ __align__(128) T tile[NSTAGE][Q][TILE];
+    __shared__ __align__(8) uint64_t bar[NSTAGE];
+    const int tid = threadIdx.x;
+    const int32_t n_tiles = S / TILE;
+    StageState ss;
+    auto issue = [&](int32_t t, int s) {
+        mbar_arrive_expect_tx(&bar[s], Q * TILE * (uint32_t)sizeof(T));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) bulk_g2s(&tile[s][i][0], pdf + i * S + t * TILE, TILE * sizeof(T), &bar[s]);
+        ss.pending |= 1u << s;
+    };
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NSTAGE; ++s) {
+            const int32_t t = blockIdx.x + s * gridDim.x;
+            if (t < n_tiles) issue(t, s);
+        }
+    }
+    int it = 0;
+    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+        const int s = it % NSTAGE;
+        const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+        const bool ok = mbar_wait_bounded(&bar[s], ph);
+        float g[Q];
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = St::raw(tile[s][i][tid]);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) latch(err, ERR_STAGE_TIMEOUT);
+            break;
+        }
+        if (tid == 0) {
+            ss.pending &= ~(1u << s);
+            ss.phase ^= 1u << s;
+            const int32_t tn = t + NSTAGE * gridDim.x;
+            if (tn < n_tiles) issue(tn, s);
+        }
+        const int32_t k = t * TILE + tid;
+        if (k < nf) {
+            collide<Q, St::scaled>(g, p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) pdf[inv(i) * S + k] = St::pack(g[i]);
+        }
+    }
+    if (tid == 0 && ss.pending) drain_stages<NSTAGE>(bar, ss);
+    __syncthreads();
 }
 
 }  // namespace slbm

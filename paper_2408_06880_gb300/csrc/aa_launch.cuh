@@ -1,10 +1,60 @@
 // aa_launch.cuh -- host dispatch of the AA kernels for one stencil size.
 #pragma once
 
+#include <mutex>
+
 #include "aa_kernels.cuh"
 #include "internal.h"
 
 namespace slbm {
+
+// Persistent grid: SMs x resident CTAs of this kernel on the current device
+// (looked up once per kernel and device).
+template <class K>
+static unsigned persistent_grid(K kernel, int threads, int64_t tiles) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int slots;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find({dev, (const void *)kernel});
+        if (it == cache.end()) {
+            int sms = 1, ctas = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kernel, threads, 0);
+            it = cache.emplace(std::make_pair(dev, (const void *)kernel), std::max(sms, 1) * std::max(ctas, 1)).first;
+        }
+        slots = it->second;
+    }
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, slots));
+}
+
+template <int Q, int ST, int TILE, int NSTAGE>
+static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    T *pdf = reinterpret_cast<T *>(d.pdf.p);
+    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
+    const CollideParams p = d.collide_params();
+    int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
+    const int64_t tiles = S / TILE;
+    if (parity == 0) {
+        auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE>;
+        k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err);
+    } else {
+        const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
+        const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
+        if (d.n_links > 0) {
+            auto k = aa_odd_staged_kernel<Q, ST, true, TILE, NSTAGE>;
+            k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, P, S, nf, maps, p, err);
+        } else {
+            auto k = aa_odd_staged_kernel<Q, ST, false, TILE, NSTAGE>;
+            k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, P, S, nf, maps, p, err);
+        }
+    }
+    return cudaGetLastError();
+}
 
 template <int Q, int ST>
 static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
@@ -12,8 +62,17 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
-    const CollideParams p = d.collide_params();
     const LaunchShape sh = d.shape[parity];
+    if (sh.variant == 1 && !d.checked && ST != ST_BF16) {
+        switch (sh.threads * 10 + sh.cells) {
+            case 642: return launch_staged<Q, ST, 64, 2>(d, parity, st);
+            case 644: return launch_staged<Q, ST, 64, 4>(d, parity, st);
+            case 1282: return launch_staged<Q, ST, 128, 2>(d, parity, st);
+            case 1284: return launch_staged<Q, ST, 128, 4>(d, parity, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    const CollideParams p = d.collide_params();
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
         switch (sh.cells) {

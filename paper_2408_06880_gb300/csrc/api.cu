@@ -79,6 +79,18 @@ CollideParams Domain::collide_params() const {
     const int s = storage == SLBM_FP32 ? 0 : scale_exp;
     p.scale = std::ldexp(1.0f, s);
     p.inv_scale = std::ldexp(1.0f, -s);
+    const double sigma = std::ldexp(1.0, s), kp = 1.0 - 0.5 * omega_p, km = 1.0 - 0.5 * omega_m;
+    p.kp = (float)kp;
+    for (int m = 0; m < MAX_PAIRS; ++m) {
+        p.alpha[m] = 0.f;
+        p.kappa[m] = 0.f;
+        if (2 * m + 1 >= q) continue;
+        const int i = 2 * m + 1;
+        const double w = q == 19 ? (double)wgt<19>(i) : (double)wgt<27>(i);
+        const double cF = cx(i) * force[0] + cy(i) * force[1] + cz(i) * force[2];
+        p.alpha[m] = (float)(sigma * kp * 9.0 * w * cF);
+        p.kappa[m] = (float)(sigma * km * 3.0 * w * cF);
+    }
     return p;
 }
 
@@ -189,6 +201,7 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     d.omega_m = s.op == SLBM_TRT ? 1.0 / (s.trt_magic / (1.0 / s.omega_plus - 0.5) + 0.5) : s.omega_plus;
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
+    if (d.storage == SLBM_FP16 && d.layout == SLBM_LAYOUT_SPARSE) d.shape[0] = LaunchShape{128, 2, 1};
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -393,15 +406,24 @@ slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_
     const Domain &d = h->d;
     if (d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "lists exist for the sparse layout only");
     cudaError_t e = cudaSuccess;
-    auto cp = [&](void *dst, const DevBuf &b, int64_t bytes) {
-        if (dst && bytes > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToHost, d.stream);
+    auto cp = [&](void *dst, const void *src, int64_t bytes) {
+        if (dst && bytes > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, d.stream);
     };
-    cp(cell_voxel, d.cell_voxel, d.n_fluid * 4);
-    cp(index_rows, d.P, (int64_t)(d.q - 1) * d.S * 4);
-    cp(link_cell, d.link_cell, d.n_links * 4);
-    cp(link_dir, d.link_dir, d.n_links * 4);
-    cp(link_type, d.link_type, d.n_links * 4);
+    cp(cell_voxel, d.cell_voxel.p, d.n_fluid * 4);
+    const int64_t pbytes = (int64_t)(d.q - 1) * d.S * 4;
+    Ctx cx = const_cast<Domain &>(d).ctx();
+    cx.held = nullptr;
+    DevBuf tmp;
+    if (index_rows && pbytes > 0) {
+        if (cx.alloc(tmp, pbytes)) return err(cx.status, g_msg);
+        e = launch_unflip(d, (int32_t *)tmp.p, d.stream);
+        cp(index_rows, tmp.p, pbytes);
+    }
+    cp(link_cell, d.link_cell.p, d.n_links * 4);
+    cp(link_dir, d.link_dir.p, d.n_links * 4);
+    cp(link_type, d.link_type.p, d.n_links * 4);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    cx.release(tmp);
     return e == cudaSuccess ? ok() : cuda_err(e, "export lists");
 }
 
@@ -435,12 +457,22 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step) {
     return ok();
 }
 
-slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells) {
+slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
-    if (threads < 32 || threads > 256 || threads % 32) return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");
-    const bool okc = parity == 0 ? (cells == 1 || cells == 2 || cells == 4) : (cells == 1 || cells == 2);
-    if (!okc) return err(SLBM_EINVAL, "cells per thread: even 1/2/4, odd 1/2");
-    h->d.shape[parity] = LaunchShape{threads, cells};
+    if (variant == 0) {
+        if (threads < 32 || threads > 256 || threads % 32)
+            return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");
+        const bool okc = parity == 0 ? (cells == 1 || cells == 2 || cells == 4) : (cells == 1 || cells == 2);
+        if (!okc) return err(SLBM_EINVAL, "cells per thread: even 1/2/4, odd 1/2");
+    } else if (variant == 1) {
+        if (h->d.layout != SLBM_LAYOUT_SPARSE || h->d.storage == SLBM_BF16)
+            return err(SLBM_EUNSUPPORTED, "the staged variant covers sparse FP32/FP16 domains");
+        if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
+            return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
+    } else {
+        return err(SLBM_EINVAL, "variant must be 0 or 1");
+    }
+    h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);
     return ok();
 }

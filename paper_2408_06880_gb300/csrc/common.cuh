@@ -48,30 +48,51 @@ __host__ __device__ __forceinline__ constexpr float wgt(int i) {
 }
 
 // --------------------------------------------------------------- storage
+// raw()/pack(): stored value <-> float in stored (scaled) units; ld()/st()
+// also remove / apply the storage scale 2^s.
 template <int ST> struct Store;
 template <> struct Store<ST_F32> {
     using T = float;
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ float raw(T v) { return v; }
+    static __device__ __forceinline__ T pack(float g) { return g; }
     static __device__ __forceinline__ float ld(T v, float) { return v; }
     static __device__ __forceinline__ T st(float g, float) { return g; }
 };
 template <> struct Store<ST_F16> {
     using T = __half;
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float raw(T v) { return __half2float(v); }
+    static __device__ __forceinline__ T pack(float g) { return __float2half_rn(g); }
     static __device__ __forceinline__ float ld(T v, float inv_scale) { return __half2float(v) * inv_scale; }
     static __device__ __forceinline__ T st(float g, float scale) { return __float2half_rn(g * scale); }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ T pack(float g) { return __float2bfloat16_rn(g); }
     static __device__ __forceinline__ float ld(T v, float inv_scale) { return __bfloat162float(v) * inv_scale; }
     static __device__ __forceinline__ T st(float g, float scale) { return __float2bfloat16_rn(g * scale); }
 };
 
 // ------------------------------------------------------------- parameters
+constexpr int MAX_PAIRS = 13;   // (27 - 1) / 2
+
 struct CollideParams {
     float omega_p;      // omega+ (= 1/tau, Eq. 7)
     float omega_m;      // omega- (TRT); equals omega_p for SRT
     float fx, fy, fz;   // body-force density
-    float scale;        // 2^s  (storage scale; 1 for FP32)
+    float scale;        // sigma = 2^s  (storage scale; 1 for FP32)
     float inv_scale;    // 2^-s
+    float kp;           // 1 - omega+/2
+    // per direction pair m (direction i = 2m+1 and its inverse i+1), in
+    // stored units: the force terms of the TRT collision that depend on the
+    // direction only (uniform body force):
+    //   alpha_m = sigma (1 - omega+/2) 9 w_i (c_i . F)
+    //   kappa_m = sigma (1 - omega-/2) 3 w_i (c_i . F)
+    float alpha[MAX_PAIRS];
+    float kappa[MAX_PAIRS];
 };
 
 // Boundary link map applied to a slot on both its read and its write in the
@@ -102,48 +123,78 @@ __device__ __forceinline__ void moments(const float (&g)[Q], float &drho, float 
     }
 }
 
-// Collision in place on shifted populations (Eq. 3).  TRT on each pair
-// (i, inverse(i)): the even part relaxes with omega+, the odd part with
-// omega-; SRT (Eq. 5) is the case omega- = omega+.  Equilibrium (Eq. 6) in
-// shifted form  g_i^eq = w_i [drho + rho (3 cu + 4.5 cu^2 - 1.5 u.u)], and the
-// Guo source S_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F split into its even
-// part w_i (9 cu cF - 3 u.F) and odd part 3 w_i cF, each weighted by
-// (1 - omega/2) of its rate.  u = (j + F/2) / rho.
-template <int Q>
+// Collision in place (Eq. 3) on shifted populations held in stored units
+// (g * sigma; sigma = 1 for FP32).  TRT on each pair (i, inverse(i)) with
+// s = g_i + g_inv and d = g_i - g_inv: the even part s/2 relaxes towards
+//   g^eq+ = w [drho + rho (4.5 cu^2 - 1.5 u.u)]    with rate omega+,
+// the odd part d/2 towards
+//   g^eq- = 3 w rho cu                              with rate omega-
+// (Eq. 6 in shifted form), plus the Guo source S = w[3(c - u) + 9 (c.u) c].F
+// split into its even part w (9 cu cF - 3 u.F) and odd part 3 w cF, each
+// weighted by (1 - omega/2) of its rate.  SRT (Eq. 5) is omega- = omega+.
+// Moments: rho = 1 + drho, drho = sum g, j = sum c g, u = (j + F/2) / rho.
+// Each fmaf is one rounding; compiled without FMA contraction the sequence
+// of roundings is fixed, so every kernel gives the same bits for a cell.
+template <int Q, bool SCALED>
 __device__ __forceinline__ void collide(float (&g)[Q], const CollideParams &p) {
-    float drho, jx, jy, jz;
-    moments<Q>(g, drho, jx, jy, jz);
+    constexpr int NP = (Q - 1) / 2;
+    float s[NP], d[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        s[m] = g[2 * m + 1] + g[2 * m + 2];
+        d[m] = g[2 * m + 1] - g[2 * m + 2];
+    }
+    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        drho += s[m];
+        const int i = 2 * m + 1;
+        if (cx(i) > 0) jx += d[m];
+        if (cx(i) < 0) jx -= d[m];
+        if (cy(i) > 0) jy += d[m];
+        if (cy(i) < 0) jy -= d[m];
+        if (cz(i) > 0) jz += d[m];
+        if (cz(i) < 0) jz -= d[m];
+    }
+    if (SCALED) {
+        drho *= p.inv_scale;
+        jx *= p.inv_scale;
+        jy *= p.inv_scale;
+        jz *= p.inv_scale;
+    }
     const float rho = 1.0f + drho;
     const float ir = 1.0f / rho;
-    const float ux = (jx + 0.5f * p.fx) * ir;
-    const float uy = (jy + 0.5f * p.fy) * ir;
-    const float uz = (jz + 0.5f * p.fz) * ir;
-    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float uF3 = 3.0f * (ux * p.fx + uy * p.fy + uz * p.fz);
-    const float kp = 1.0f - 0.5f * p.omega_p;
-    const float km = 1.0f - 0.5f * p.omega_m;
+    const float ux = fmaf(0.5f, p.fx, jx) * ir;
+    const float uy = fmaf(0.5f, p.fy, jy) * ir;
+    const float uz = fmaf(0.5f, p.fz, jz) * ir;
+    const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+    const float uF = fmaf(uz, p.fz, fmaf(uy, p.fy, ux * p.fx));
+    const float E = fmaf(-1.5f * rho, usq, drho);              // drho - 1.5 rho u.u
+    const float sr = SCALED ? p.scale * rho : rho;              // sigma rho
+    const float sE = SCALED ? p.scale * E : E;                  // sigma (drho - 1.5 rho u.u)
+    const float skF = SCALED ? p.scale * (p.kp * 3.0f * uF) : p.kp * 3.0f * uF;  // sigma kp 3 u.F
     // rest population: even only
     {
-        const float w = wgt<Q>(0);
-        const float eq = w * (drho - rho * usq15);
-        g[0] += -p.omega_p * (g[0] - eq) + kp * (-w * uF3);
+        constexpr float w = wgt<Q>(0);
+        g[0] = fmaf(p.omega_p, fmaf(w, sE, -g[0]), g[0]) - w * skF;
     }
 #pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const int b = i + 1;
+    for (int m = 0; m < NP; ++m) {
+        const int i = 2 * m + 1;
         const float w = wgt<Q>(i);
-        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float cF = cx(i) * p.fx + cy(i) * p.fy + cz(i) * p.fz;
-        const float eqp = w * (drho + rho * (4.5f * cu * cu - usq15));
-        const float eqm = w * rho * 3.0f * cu;
-        const float sp = w * (9.0f * cu * cF - uF3);
-        const float sm = 3.0f * w * cF;
-        const float gp = 0.5f * (g[i] + g[b]);
-        const float gm = 0.5f * (g[i] - g[b]);
-        const float dp = -p.omega_p * (gp - eqp) + kp * sp;
-        const float dm = -p.omega_m * (gm - eqm) + km * sm;
-        g[i] += dp + dm;
-        g[b] += dp - dm;
+        float cu = 0.f;
+        if (cx(i) > 0) cu += ux;
+        if (cx(i) < 0) cu -= ux;
+        if (cy(i) > 0) cu += uy;
+        if (cy(i) < 0) cu -= uy;
+        if (cz(i) > 0) cu += uz;
+        if (cz(i) < 0) cu -= uz;
+        const float eqp = fmaf((4.5f * w) * sr, cu * cu, w * sE);   // sigma g^eq+
+        const float eqm = ((3.0f * w) * sr) * cu;                   // sigma g^eq-
+        const float dp = fmaf(p.omega_p, fmaf(-0.5f, s[m], eqp), fmaf(p.alpha[m], cu, -(w * skF)));
+        const float dm = fmaf(p.omega_m, fmaf(-0.5f, d[m], eqm), p.kappa[m]);
+        g[i] = g[i] + (dp + dm);
+        g[i + 1] = g[i + 1] + (dp - dm);
     }
 }
 
@@ -160,10 +211,11 @@ __device__ __forceinline__ void equilibrium_shifted(float rho, float ux, float u
     }
 }
 
-// AA odd-step slot of direction i for cell k from its pull entry e >= 0
-// (Sec. 5.1): the entry lies in row i (fluid neighbour n: e = i*S + n) or in
-// row inverse(i) (wall: e = inverse(i)*S + k).  The odd step reads f_i(x_k)
-// from the same column with the row flipped: inverse(i)*S + n, resp. i*S + k.
+// Row flip between i and inverse(i) of a slot e >= 0 in one of those two rows
+// (Sec. 5.1).  A pull entry P(i,k) lies in row i (fluid neighbour n:
+// i*S + n) or in row inverse(i) (wall: inverse(i)*S + k); the AA odd step
+// reads f_i(x_k) from the same column with the row flipped.  The flip is an
+// involution, so it also maps the odd-step slot back to the pull entry.
 __device__ __forceinline__ int32_t flip_row(int32_t e, int i, int32_t S) {
     if (i & 1) return e < (i + 1) * S ? e + S : e - S;   // inverse = i+1
     return e >= i * S ? e - S : e + S;                    // inverse = i-1

@@ -53,10 +53,10 @@ __global__ void __launch_bounds__(128) dense_even_kernel(typename Store<ST>::T *
     if (v >= n || !(mask[v] >> 31)) return;
     float g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = St::ld(pdf[i * S + v], p.inv_scale);
-    collide<Q>(g, p);
+    for (int i = 0; i < Q; ++i) g[i] = St::raw(pdf[i * S + v]);
+    collide<Q, St::scaled>(g, p);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) pdf[inv(i) * S + v] = St::st(g[i], p.scale);
+    for (int i = 0; i < Q; ++i) pdf[inv(i) * S + v] = St::pack(g[i]);
 }
 
 // grid (ceil(nx/blockDim), ny, nz): no divisions to find the coordinates.
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
     if (!(m >> 31)) return;
     int64_t R[Q];
     float g[Q];
-    g[0] = St::ld(pdf[v], p.inv_scale);
+    g[0] = St::raw(pdf[v]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (m >> i & 1u) {
@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
             zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
             R[i] = inv(i) * S + xn + nx * (yn + ny * zn);
         }
-        g[i] = St::ld(pdf[R[i]], p.inv_scale);
+        g[i] = St::raw(pdf[R[i]]);
     }
-    collide<Q>(g, p);
-    pdf[v] = St::st(g[0], p.scale);
+    collide<Q, St::scaled>(g, p);
+    pdf[v] = St::pack(g[0]);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) pdf[R[i]] = St::st(g[inv(i)], p.scale);
+    for (int i = 1; i < Q; ++i) pdf[R[i]] = St::pack(g[inv(i)]);
 }
 
 int build_dense_mask(Ctx &cx, Domain &d, const uint8_t *d_flags) {

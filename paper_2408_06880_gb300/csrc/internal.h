@@ -34,9 +34,13 @@ struct Ctx {
     void fail(slbm_status s, const char *msg);
 };
 
+// variant 0: one thread per `cells` consecutive cells, `threads` per block.
+// variant 1: persistent CTAs of `threads` (= tile) cells with `cells` (=
+// pipeline stages) bulk-staged tiles in flight.
 struct LaunchShape {
     int32_t threads;
     int32_t cells;
+    int32_t variant;
 };
 
 struct Domain {
@@ -50,7 +54,7 @@ struct Domain {
     int64_t n_fluid = 0, S = 0, n_links = 0, step = 0;
     // device data
     DevBuf pdf;                        // Q x S stored populations
-    DevBuf P;                          // (Q-1) x S pull entries (sparse)
+    DevBuf P;                          // (Q-1) x S odd-step slots R(i,k) (row-flipped pull entries)
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf mask;                       // per-voxel link mask (dense)
@@ -63,7 +67,7 @@ struct Domain {
     slbm_allocator hook{};
     bool has_hook = false;
     int64_t device_bytes = 0;
-    LaunchShape shape[2] = {{256, 2}, {256, 1}};
+    LaunchShape shape[2] = {{64, 2, 0}, {64, 1, 0}};
     bool checked = false;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, parity) -> exec
 
@@ -85,6 +89,7 @@ constexpr int RED_CELLS_PER_THREAD = 8;
 constexpr int RED_CHUNK = RED_THREADS * RED_CELLS_PER_THREAD;
 
 // lists.cu
+cudaError_t launch_unflip(const Domain &d, int32_t *out, cudaStream_t st);
 int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
                        int64_t n_inlet_u);
 // stream_collide.cu

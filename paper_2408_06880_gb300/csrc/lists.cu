@@ -205,8 +205,13 @@ __device__ __forceinline__ int64_t inlet_rank(const int32_t *list, int64_t n, in
     return (lo < n && list[lo] == v) ? lo : -1;
 }
 
-// One thread per cell; writes its Q-1 pull entries (column k of each row) and
-// its boundary links.  Link maps are in shifted, unscaled units.
+// One thread per cell; writes its Q-1 entries (column k of each row) and its
+// boundary links.  The canonical pull entry P(i,k) (Sec. 3.1: fluid
+// neighbour -> i*S + n, wall -> inverse(i)*S + k, inlet/outlet -> -(b+1)) is
+// stored in the form the AA odd step reads: non-negative entries with their
+// row flipped (flip_row), i.e. the odd-step slot R(i,k).  The flip is exact
+// and its own inverse; sparse_lbm_export_lists flips back to P.  Link maps are
+// in shifted, unscaled units.
 template <int Q>
 __global__ void build_index(Box b, const uint8_t *flags, const int32_t *cell_id,
                             const int32_t *cell_voxel, int32_t nf, int32_t S, int32_t *P,
@@ -257,8 +262,27 @@ __global__ void build_index(Box b, const uint8_t *flags, const int32_t *cell_id,
             }
             maps[l] = m;
         }
-        P[(int64_t)(i - 1) * S + k] = e;
+        P[(int64_t)(i - 1) * S + k] = e >= 0 ? flip_row(e, i, S) : e;
     }
+}
+
+// Odd-step slots -> canonical pull entries (the inverse of the flip above),
+// into a separate buffer for export.
+__global__ void unflip_rows(const int32_t *R, int32_t S, int32_t rows, int32_t *P) {
+    const int64_t n = (int64_t)rows * S;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = R[j];
+        const int i = (int)(j / S) + 1;
+        P[j] = e >= 0 ? flip_row(e, i, S) : e;
+    }
+}
+
+cudaError_t launch_unflip(const Domain &d, int32_t *out, cudaStream_t st) {
+    const int64_t n = (int64_t)(d.q - 1) * d.S;
+    if (n == 0) return cudaSuccess;
+    unflip_rows<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, st>>>(
+        (const int32_t *)d.P.p, (int32_t)d.S, d.q - 1, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- driver

@@ -3,7 +3,7 @@
 //
 // The state is read at either AA parity: after an even number of steps the
 // field is natural (row i of column k); after an odd number the populations
-// of cell k sit in the odd-step slots R(i,k) (the row-flipped pull entries),
+// of cell k sit in the odd-step slots R(i,k) that the device index-list holds,
 // so reading them is the gather half of the odd kernel.
 //
 // The sums are deterministic: cells are cut into fixed chunks of RED_CHUNK
@@ -33,7 +33,7 @@ struct SparseView {
                 g[i] = St::ld(pdf[i * S + k], inv_scale);
             } else {
                 const int32_t e = P[(i - 1) * S + k];
-                const int32_t r = e >= 0 ? flip_row(e, i, S) : i * S + k;
+                const int32_t r = e >= 0 ? e : i * S + k;
                 float v = St::ld(pdf[r], inv_scale);
                 if (e < 0) {
                     const LinkMap m = maps[-(e + 1)];

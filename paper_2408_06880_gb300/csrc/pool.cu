@@ -1,16 +1,670 @@
-// pool.cu -- batched stepping of many domains (filled in below).
+// pool.cu -- batched stepping of many sparse domains with one persistent
+// kernel per time step (the method's AA update, Sec. 5.1, over the
+// concatenation of the member domains' compacted cell lists).
+//
+// The pool keeps a device table of its members, sorted by their first global
+// tile: PDF-list, odd-step slot list, link maps, stride, cell count, tile
+// offset, the parity of the member at the start of the current launch
+// sequence, and the member's collision constants.  A launch splits the global
+// tiles (blockDim cells each) into one contiguous range per CTA of a
+// persistent grid; the member owning a tile decides, by its parity, between
+// the cell-local even update and the index-driven odd update.  Members at
+// different parities share a launch.
+//
+// Two launch variants.  Persistent walker (ctas_per_sm > 0): the grid size and
+// the table address never change, so a captured CUDA graph of K launches
+// stays valid when members join or leave; the host rewrites the table
+// (stream-ordered) instead.  Tile grid (default): one CTA per tile, from
+// per-tile descriptors; its graphs are re-captured after membership changes.  A host-mapped abort word is polled every
+// few tiles; a raised flag makes every CTA stop early and the next
+// synchronising pool call reports SLBM_EABORTED.
+#include <cstring>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "aa_kernels.cuh"
 #include "internal.h"
 
+namespace slbm {
+
+struct PoolEntry {
+    void *pdf;
+    const int32_t *R;
+    const LinkMap *maps;
+    int32_t S, nf, n_links, tile_begin, n_tiles, parity0;
+    CollideParams p;
+};
+
+struct PoolHeader {
+    int32_t n_dom, total_tiles;
+};
+
+template <int Q, int ST>
+__device__ __forceinline__ void even_cell(typename Store<ST>::T *__restrict__ pdf, int32_t S, int32_t k,
+                                          const CollideParams &p) {
+    using St = Store<ST>;
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = St::raw(pdf[i * S + k]);
+    collide<Q, St::scaled>(g, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pdf[inv(i) * S + k] = St::pack(g[i]);
+}
+
+// Each CTA takes one contiguous range of global tiles, so it changes member
+// rarely: the member entry is found once by binary search and then followed
+// forward, and copied into shared memory only when the member changes.  The
+// host-mapped abort word is read every ABORT_POLL tiles.
+constexpr int ABORT_POLL = 32;
+
+// PARITY 0 / 1: every member is at that parity in this launch (the common
+// case: members join at step 0 and are stepped in even chunks); -1: each
+// member's own parity decides per tile.  UNI: every member has the same
+// collision constants, passed as the kernel parameter `up` (read from the
+// constant bank) instead of from the shared-memory copy of the entry.
+template <int Q, int ST, int PARITY, bool UNI>
+__global__ void __launch_bounds__(128, 4) pool_step_kernel(const PoolHeader *__restrict__ hdr,
+                                                        const PoolEntry *__restrict__ tab, int32_t seq_step,
+                                                        const volatile int32_t *abort_flag, int32_t *status,
+                                                        const __grid_constant__ CollideParams up) {
+    using T = typename Store<ST>::T;
+    __shared__ PoolEntry sE;
+    __shared__ int32_t s_dom, s_next, s_stop;
+    const int32_t n_dom = hdr->n_dom, total = hdr->total_tiles;
+    const int tile = blockDim.x;
+    const int32_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int32_t t_lo = blockIdx.x * per, t_hi = min(total, t_lo + per);
+    if (t_lo >= t_hi) return;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_dom - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].tile_begin <= t_lo) lo = mid;
+            else hi = mid - 1;
+        }
+        s_dom = lo;
+        s_next = lo + 1 < n_dom ? tab[lo + 1].tile_begin : total;
+        s_stop = 0;
+    }
+    __syncthreads();
+    constexpr int words = (int)(sizeof(PoolEntry) / 4);
+    {   // cooperative copy of the first member entry
+        const int32_t *src = reinterpret_cast<const int32_t *>(&tab[s_dom]);
+        int32_t *dst = reinterpret_cast<int32_t *>(&sE);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int32_t t = t_lo; t < t_hi; ++t) {
+        if (t >= s_next) {            // crossed into the next member (uniform)
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int d = s_dom;
+                while (d + 1 < n_dom && tab[d + 1].tile_begin <= t) ++d;
+                s_dom = d;
+                s_next = d + 1 < n_dom ? tab[d + 1].tile_begin : total;
+            }
+            __syncthreads();
+            const int32_t *src = reinterpret_cast<const int32_t *>(&tab[s_dom]);
+            int32_t *dst = reinterpret_cast<int32_t *>(&sE);
+            for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+        }
+        if (((t - t_lo) % ABORT_POLL) == 0) {
+            if (threadIdx.x == 0 && abort_flag && *abort_flag) {
+                atomicCAS(status, 0, (int32_t)SLBM_EABORTED);
+                s_stop = 1;
+            }
+            __syncthreads();
+            if (s_stop) break;
+        }
+        const int32_t S = sE.S;
+        const int32_t k = (t - sE.tile_begin) * tile + threadIdx.x;
+        if (k < sE.nf) {
+            T *pdf = reinterpret_cast<T *>(sE.pdf);
+            const int parity = PARITY >= 0 ? PARITY : ((sE.parity0 + seq_step) & 1);
+            if (parity == 0) {
+                if constexpr (UNI) even_cell<Q, ST>(pdf, S, k, up);
+                else even_cell<Q, ST>(pdf, S, k, sE.p);
+            } else {
+                const int32_t *R = sE.R;
+                int32_t e[Q];
+                e[0] = 0;
+#pragma unroll
+                for (int i = 1; i < Q; ++i) e[i] = __ldcs(R + (i - 1) * S + k);
+                // one link-aware path: members without inlet/outlet links
+                // never take its branch
+                if constexpr (UNI) odd_cell<Q, ST, true>(pdf, e, k, S, sE.maps, up);
+                else odd_cell<Q, ST, true>(pdf, e, k, S, sE.maps, sE.p);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile-grid variant (the default): one CTA per tile of the concatenated cell
+// lists.  Each tile has a 32-byte descriptor (PDF-list, slot list, stride,
+// cell count, first cell, member) built on the device when the membership
+// changes; a CTA reads it with one uniform load and starts on its cells.  Two
+// tilings: 256-cell tiles for the cell-local even step (128 threads x 2
+// consecutive cells, vector accesses) and 128-cell tiles for the odd step and
+// for launches that mix parities (128 threads x 1 cell).  Every 256th CTA
+// reads the host-mapped abort word and raises a device stop word that all
+// CTAs read before starting.
+constexpr int POOL_THREADS = 128;
+
+struct TileDesc {
+    void *pdf;
+    const int32_t *R;
+    int32_t S, nf, first, member;
+};
+
+__global__ void fill_tiles(const PoolEntry *__restrict__ tab, int32_t n_dom, int32_t cells_per_tile,
+                           const int32_t *__restrict__ begin, TileDesc *__restrict__ out) {
+    const int32_t d = blockIdx.y;
+    if (d >= n_dom) return;
+    const PoolEntry &E = tab[d];
+    const int32_t n = (E.nf + cells_per_tile - 1) / cells_per_tile, b = begin[d];
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        TileDesc D;
+        D.pdf = E.pdf;
+        D.R = E.R;
+        D.S = E.S;
+        D.nf = E.nf;
+        D.first = t * cells_per_tile;
+        D.member = d;
+        out[b + t] = D;
+    }
+}
+
+// PARITY: 0 / 1 uniform, -1 mixed (per member, from its table row).
+// UNI: uniform collision constants in `up`.  BC: handle inlet/outlet links.
+// CPT: cells per thread (2 only for the uniform even step).
+template <int Q, int ST, int PARITY, bool UNI, bool BC, int CPT>
+__global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry *__restrict__ tab,
+                                                                 const TileDesc *__restrict__ tiles,
+                                                                 int32_t seq_step,
+                                                                 const volatile int32_t *abort_flag,
+                                                                 int32_t *stop,
+                                                                 const __grid_constant__ CollideParams up) {
+    using St = Store<ST>;
+    using T = typename St::T;
+    const int32_t t = blockIdx.x;
+    int32_t halt = *(volatile int32_t *)stop;
+    if (!halt && (t & 255) == 0 && abort_flag && *abort_flag) {
+        if (threadIdx.x == 0) atomicCAS(stop, 0, (int32_t)SLBM_EABORTED);
+        halt = 1;
+    }
+    if (halt) return;
+    const TileDesc D = tiles[t];
+    const CollideParams &p = UNI ? up : tab[D.member].p;
+    T *pdf = reinterpret_cast<T *>(D.pdf);
+    const int32_t S = D.S, nf = D.nf;
+    int parity = PARITY;
+    if (PARITY < 0) parity = (tab[D.member].parity0 + seq_step) & 1;
+    if (parity == 0) {
+        const int32_t k0 = D.first + CPT * threadIdx.x;
+        if (k0 >= nf) return;
+        float g[CPT][Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + i * S + k0);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) g[c][i] = St::raw(x.v[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+        const bool full = k0 + CPT <= nf;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            Vec<T, CPT> y;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(g[c][i]);
+            T *dst = pdf + inv(i) * S + k0;
+            if (full) {
+                st_vec<T, CPT>(dst, y);
+            } else {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (k0 + c < nf) dst[c] = y.v[c];
+            }
+        }
+    } else {
+        const int32_t k = D.first + threadIdx.x;
+        if (k >= nf) return;
+        int32_t e[Q];
+        e[0] = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) e[i] = __ldcs(D.R + (i - 1) * S + k);
+        // members without links never take the link branch of the BC path
+        odd_cell<Q, ST, BC>(pdf, e, k, S, BC ? tab[D.member].maps : nullptr, p);
+    }
+}
+
+using TileKernel = void (*)(const PoolEntry *, const TileDesc *, int32_t, const volatile int32_t *, int32_t *,
+                            const CollideParams);
+
+// mode: 0 mixed parity, 1 + 2*parity + uni
+template <int Q, int ST>
+static TileKernel tile_kernel_st(int mode, bool bc) {
+    switch (mode) {
+        case 1: return pool_tile_kernel<Q, ST, 0, false, false, 2>;
+        case 2: return pool_tile_kernel<Q, ST, 0, true, false, 2>;
+        case 3: return bc ? pool_tile_kernel<Q, ST, 1, false, true, 1> : pool_tile_kernel<Q, ST, 1, false, false, 1>;
+        case 4: return bc ? pool_tile_kernel<Q, ST, 1, true, true, 1> : pool_tile_kernel<Q, ST, 1, true, false, 1>;
+        default: return pool_tile_kernel<Q, ST, -1, false, true, 1>;
+    }
+}
+
+template <int Q>
+static TileKernel tile_kernel_for(int storage, int mode, bool bc) {
+    switch (storage) {
+        case SLBM_FP32: return tile_kernel_st<Q, ST_F32>(mode, bc);
+        case SLBM_FP16: return tile_kernel_st<Q, ST_F16>(mode, bc);
+        default: return tile_kernel_st<Q, ST_BF16>(mode, bc);
+    }
+}
+
+using PoolKernel = void (*)(const PoolHeader *, const PoolEntry *, int32_t, const volatile int32_t *, int32_t *,
+                            const CollideParams);
+
+// mode: 0 generic, 1 + 2*parity + uni (parity-uniform variants)
+template <int Q, int ST>
+static PoolKernel pool_kernel_st(int mode) {
+    switch (mode) {
+        case 1: return pool_step_kernel<Q, ST, 0, false>;
+        case 2: return pool_step_kernel<Q, ST, 0, true>;
+        case 3: return pool_step_kernel<Q, ST, 1, false>;
+        case 4: return pool_step_kernel<Q, ST, 1, true>;
+        default: return pool_step_kernel<Q, ST, -1, false>;
+    }
+}
+
+template <int Q>
+static PoolKernel pool_kernel_for(int storage, int mode) {
+    switch (storage) {
+        case SLBM_FP32: return pool_kernel_st<Q, ST_F32>(mode);
+        case SLBM_FP16: return pool_kernel_st<Q, ST_F16>(mode);
+        default: return pool_kernel_st<Q, ST_BF16>(mode);
+    }
+}
+
+}  // namespace slbm
+
+using namespace slbm;
+
+struct slbm_pool {
+    int32_t q = 19, storage = SLBM_FP32, capacity = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<slbm_t *> members;       // by slot; nullptr = free
+    std::vector<PoolEntry> host_tab;     // staged table (active members, sorted)
+    std::vector<int32_t> order;          // slot of each table row
+    PoolHeader host_hdr{0, 0};
+    void *d_tab = nullptr, *d_hdr = nullptr, *d_status = nullptr, *d_red = nullptr;
+    TileDesc *d_tiles[2] = {nullptr, nullptr};   // tile descriptors: [0] 256-cell, [1] 128-cell tiles
+    int64_t tiles_cap[2] = {0, 0};
+    int32_t n_tiles[2] = {0, 0};
+    int32_t *d_begin = nullptr;                  // per-row first tile (scratch for the fill)
+    int32_t *h_abort = nullptr;          // host-mapped abort word
+    int32_t *d_abort = nullptr;
+    bool dirty = true;
+    int32_t threads = 64, ctas_per_sm = 0;   // ctas_per_sm > 0: persistent walker
+    unsigned grid[5] = {0, 0, 0, 0, 0};      // persistent grid of each kernel variant
+    int32_t p0 = -1;                     // common parity of all members, or -1
+    bool uni = false;                    // all members share collision constants
+    bool any_links = false;              // some member has inlet/outlet links
+    CollideParams up{};                  // those constants
+    // (k, p0, uni) -> exec; the uniform constants a graph was captured with
+    std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, CollideParams>> graphs;
+};
+
+namespace {
+
+slbm_status perr(slbm_status s, const std::string &m) {
+    set_error(s, m);
+    return s;
+}
+
+slbm_status pcuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return perr(SLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void drop_pool_graphs(slbm_pool *p) {
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second.first);
+    p->graphs.clear();
+}
+
+PoolKernel kernel_of(const slbm_pool *p, int mode) {
+    return p->q == 19 ? pool_kernel_for<19>(p->storage, mode) : pool_kernel_for<27>(p->storage, mode);
+}
+
+// Persistent grid of each variant: SMs x its resident CTAs (capped by
+// ctas_per_sm).  It depends on the variant only, never on the membership.
+slbm_status size_grid(slbm_pool *p) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int mode = 0; mode <= 4; ++mode) {
+        int c = 1;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel_of(p, mode), p->threads, 0);
+        if (e != cudaSuccess) return pcuda(e, "occupancy");
+        c = std::max(c, 1);
+        if (p->ctas_per_sm > 0) c = std::min(c, p->ctas_per_sm);
+        p->grid[mode] = (unsigned)(std::max(sms, 1) * c);
+    }
+    return SLBM_OK;
+}
+
+// Rebuild and upload the table (stream-ordered) when membership or parities
+// changed.
+slbm_status sync_table(slbm_pool *p) {
+    for (size_t r = 0; r < p->order.size() && !p->dirty; ++r)   // a member stepped outside the pool
+        if (p->members[p->order[r]] && (int32_t)(p->members[p->order[r]]->d.step & 1) != p->host_tab[r].parity0)
+            p->dirty = true;
+    if (!p->dirty) return SLBM_OK;
+    p->host_tab.clear();
+    p->order.clear();
+    int32_t tile = 0;
+    for (int32_t s = 0; s < p->capacity; ++s) {
+        slbm_t *h = p->members[s];
+        if (!h) continue;
+        const Domain &d = h->d;
+        PoolEntry E{};
+        E.pdf = d.pdf.p;
+        E.R = (const int32_t *)d.P.p;
+        E.maps = (const LinkMap *)d.link_map.p;
+        E.S = (int32_t)d.S;
+        E.nf = (int32_t)d.n_fluid;
+        E.n_links = (int32_t)d.n_links;
+        const int32_t tcells = p->ctas_per_sm > 0 ? p->threads : POOL_THREADS;
+        E.n_tiles = (int32_t)((d.n_fluid + tcells - 1) / tcells);
+        E.tile_begin = tile;
+        E.parity0 = (int32_t)(d.step & 1);
+        E.p = d.collide_params();
+        if (E.n_tiles == 0) continue;
+        tile += E.n_tiles;
+        p->host_tab.push_back(E);
+        p->order.push_back(s);
+    }
+    p->host_hdr = PoolHeader{(int32_t)p->host_tab.size(), tile};
+    p->p0 = p->host_tab.empty() ? 0 : p->host_tab[0].parity0;
+    p->uni = !p->host_tab.empty();
+    p->any_links = false;
+    for (const PoolEntry &E : p->host_tab) {
+        if (E.n_links > 0) p->any_links = true;
+        if (E.parity0 != p->p0) p->p0 = -1;
+        if (std::memcmp(&E.p, &p->host_tab[0].p, sizeof(CollideParams)) != 0) p->uni = false;
+    }
+    p->up = p->host_tab.empty() ? CollideParams{} : p->host_tab[0].p;
+    cudaError_t e = cudaSuccess;
+    if (!p->host_tab.empty())
+        e = cudaMemcpyAsync(p->d_tab, p->host_tab.data(), p->host_tab.size() * sizeof(PoolEntry),
+                            cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_hdr, &p->host_hdr, sizeof(PoolHeader), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && p->ctas_per_sm == 0 && tile > 0) {
+        // tile descriptors for both tilings
+        const int32_t cells[2] = {2 * POOL_THREADS, POOL_THREADS};
+        std::vector<int32_t> begin(p->host_tab.size());
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            int32_t n = 0;
+            for (size_t r = 0; r < p->host_tab.size(); ++r) {
+                begin[r] = n;
+                n += (p->host_tab[r].nf + cells[v] - 1) / cells[v];
+            }
+            p->n_tiles[v] = n;
+            if (n > p->tiles_cap[v]) {
+                if (p->d_tiles[v]) cudaFree(p->d_tiles[v]);
+                p->d_tiles[v] = nullptr;
+                e = cudaMalloc(&p->d_tiles[v], (size_t)n * sizeof(TileDesc));
+                p->tiles_cap[v] = e == cudaSuccess ? n : 0;
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p->d_begin, begin.data(), begin.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, p->stream);
+            if (e == cudaSuccess) {
+                fill_tiles<<<dim3(64, (unsigned)p->host_tab.size()), 256, 0, p->stream>>>(
+                    (const PoolEntry *)p->d_tab, (int32_t)p->host_tab.size(), cells[v], p->d_begin, p->d_tiles[v]);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);   // `begin` is reused
+        }
+    }
+    // pageable source: make sure the copy has consumed the staging arrays
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pcuda(e, "pool table upload");
+    if (p->ctas_per_sm == 0) drop_pool_graphs(p);   // the tile grid follows the membership
+    p->dirty = false;
+    return SLBM_OK;
+}
+
+cudaError_t launch_seq(slbm_pool *p, int32_t k) {
+    for (int32_t t = 0; t < k; ++t) {
+        const int mode = p->p0 < 0 ? 0 : 1 + 2 * ((p->p0 + t) & 1) + (p->uni ? 1 : 0);
+        if (p->ctas_per_sm == 0) {
+            TileKernel tk = p->q == 19 ? tile_kernel_for<19>(p->storage, mode, p->any_links)
+                                       : tile_kernel_for<27>(p->storage, mode, p->any_links);
+            const int v = (mode == 1 || mode == 2) ? 0 : 1;      // uniform even step: 256-cell tiles
+            if (p->n_tiles[v] == 0) continue;
+            tk<<<(unsigned)p->n_tiles[v], POOL_THREADS, 0, p->stream>>>(
+                (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        PoolKernel kern = kernel_of(p, mode);
+        kern<<<p->grid[mode], p->threads, 0, p->stream>>>((const PoolHeader *)p->d_hdr, (const PoolEntry *)p->d_tab, t,
+                                                    p->d_abort, (int32_t *)p->d_status, p->up);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
 extern "C" {
-slbm_status slbm_pool_create(int32_t, int32_t, int32_t, void *, slbm_pool_t **out) {
-    if (out) *out = nullptr;
-    slbm::set_error(SLBM_EUNSUPPORTED, "pool not built");
-    return SLBM_EUNSUPPORTED;
+
+slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream, slbm_pool_t **out) {
+    if (!out) return perr(SLBM_EINVAL, "out must be non-NULL");
+    *out = nullptr;
+    if (q != 19 && q != 27) return perr(SLBM_EINVAL, "q must be 19 or 27");
+    if (storage < SLBM_FP32 || storage > SLBM_BF16) return perr(SLBM_EINVAL, "bad storage");
+    if (capacity < 1 || capacity > 65536) return perr(SLBM_EINVAL, "capacity must be 1..65536");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return perr(SLBM_ECUDA, "no CUDA device available (there is no CPU fallback)");
+    }
+    slbm_pool *p = new slbm_pool();
+    p->q = q;
+    p->storage = storage;
+    p->capacity = capacity;
+    p->members.assign(capacity, nullptr);
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        p->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreate(&p->stream);
+        p->own_stream = true;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tab, (size_t)capacity * sizeof(PoolEntry));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_hdr, sizeof(PoolHeader));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_red, (size_t)capacity * 5 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_begin, (size_t)capacity * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&p->h_abort, sizeof(int32_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *p->h_abort = 0;
+        e = cudaHostGetDevicePointer((void **)&p->d_abort, p->h_abort, 0);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_hdr, 0, sizeof(PoolHeader), p->stream);
+    slbm_status st = e == cudaSuccess ? size_grid(p) : pcuda(e, "pool create");
+    if (st == SLBM_OK) {
+        e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) st = pcuda(e, "pool create sync");
+    }
+    if (st != SLBM_OK) {
+        const std::string m = sparse_lbm_last_error();
+        slbm_pool_free(p);
+        return perr(st, m);
+    }
+    *out = p;
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
 }
-slbm_status slbm_pool_add(slbm_pool_t *, slbm_t *, int32_t *) { return SLBM_EUNSUPPORTED; }
-slbm_status slbm_pool_remove(slbm_pool_t *, int32_t) { return SLBM_EUNSUPPORTED; }
-slbm_status slbm_pool_step(slbm_pool_t *, int32_t, int32_t) { return SLBM_EUNSUPPORTED; }
-slbm_status slbm_pool_reduce(slbm_pool_t *, double *, int32_t) { return SLBM_EUNSUPPORTED; }
-slbm_status slbm_pool_set_launch(slbm_pool_t *, int32_t, int32_t) { return SLBM_EUNSUPPORTED; }
-void slbm_pool_free(slbm_pool_t *) {}
+
+slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot) {
+    if (!p || !h || !slot) return perr(SLBM_EINVAL, "null argument");
+    const Domain &d = h->d;
+    if (d.layout != SLBM_LAYOUT_SPARSE) return perr(SLBM_EUNSUPPORTED, "pool members must use the sparse layout");
+    if (d.q != p->q || d.storage != p->storage) return perr(SLBM_EINVAL, "member q / storage differ from the pool's");
+    for (int32_t s = 0; s < p->capacity; ++s)
+        if (p->members[s] == h) return perr(SLBM_EINVAL, "domain is already a member");
+    for (int32_t s = 0; s < p->capacity; ++s) {
+        if (!p->members[s]) {
+            // order the domain's own stream before the pool's
+            cudaStreamSynchronize(d.stream);
+            p->members[s] = h;
+            p->dirty = true;
+            *slot = s;
+            set_error(SLBM_OK, "");
+            return SLBM_OK;
+        }
+    }
+    return perr(SLBM_ENOMEM, "pool is full");
 }
+
+slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot) {
+    if (!p || slot < 0 || slot >= p->capacity || !p->members[slot]) return perr(SLBM_EINVAL, "bad slot");
+    const cudaError_t e = cudaStreamSynchronize(p->stream);   // member work done before it leaves
+    p->members[slot] = nullptr;
+    p->dirty = true;
+    if (e != cudaSuccess) return pcuda(e, "pool remove");
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph) {
+    if (!p || k < 0) return perr(SLBM_EINVAL, "need a pool and k >= 0");
+    if (k == 0) {
+        set_error(SLBM_OK, "");
+        return SLBM_OK;
+    }
+    slbm_status st = sync_table(p);
+    if (st != SLBM_OK) return st;
+    if (p->host_hdr.total_tiles > 0) {
+        cudaError_t e;
+        if (use_graph) {
+            const auto key = std::make_tuple((int)k, (int)p->p0, (p->uni ? 1 : 0) + (p->any_links ? 2 : 0));
+            auto it = p->graphs.find(key);
+            if (it != p->graphs.end() && p->uni &&
+                std::memcmp(&it->second.second, &p->up, sizeof(CollideParams)) != 0) {
+                cudaGraphExecDestroy(it->second.first);     // captured with other constants
+                p->graphs.erase(it);
+                it = p->graphs.end();
+            }
+            if (it == p->graphs.end()) {
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) return pcuda(e, "begin capture");
+                const cudaError_t le = launch_seq(p, k);
+                e = cudaStreamEndCapture(p->stream, &g);
+                if (le != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return pcuda(le, "pool launch during capture");
+                }
+                if (e != cudaSuccess) return pcuda(e, "end capture");
+                cudaGraphExec_t ex = nullptr;
+                e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return pcuda(e, "graph instantiate");
+                it = p->graphs.emplace(key, std::make_pair(ex, p->up)).first;
+            }
+            e = cudaGraphLaunch(it->second.first, p->stream);
+        } else {
+            e = launch_seq(p, k);
+        }
+        if (e != cudaSuccess) return pcuda(e, "pool step");
+    }
+    for (int32_t s = 0; s < p->capacity; ++s)
+        if (p->members[s] && p->members[s]->d.n_fluid > 0) p->members[s]->d.step += k;
+    if (k & 1) p->dirty = true;   // parities flipped
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem) {
+    if (!p || !out) return perr(SLBM_EINVAL, "null argument");
+    if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return perr(SLBM_EINVAL, "bad mem");
+    cudaError_t e = cudaSuccess;
+    double *dev_out = mem == SLBM_MEM_HOST ? (double *)p->d_red : out;
+    const size_t bytes = (size_t)p->capacity * 5 * sizeof(double);
+    e = cudaMemsetAsync(dev_out, 0, bytes, p->stream);
+    for (int32_t s = 0; s < p->capacity && e == cudaSuccess; ++s) {
+        slbm_t *h = p->members[s];
+        if (h) e = launch_reduce(h->d, dev_out + 5 * s, p->stream);
+    }
+    int32_t status = 0;
+    if (e == cudaSuccess && mem == SLBM_MEM_HOST) {
+        e = cudaMemcpyAsync(out, dev_out, bytes, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    if (e != cudaSuccess) return pcuda(e, "pool reduce");
+    if (status == SLBM_EABORTED) return perr(SLBM_EABORTED, "a pool launch was aborted by the host flag");
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm) {
+    if (!p) return perr(SLBM_EINVAL, "null pool");
+    if (threads < 32 || threads > 128 || threads % 32) return perr(SLBM_EINVAL, "threads must be 32..128, multiple of 32");
+    if (ctas_per_sm < 0) return perr(SLBM_EINVAL, "ctas_per_sm must be >= 0");
+    p->threads = threads;
+    p->ctas_per_sm = ctas_per_sm;
+    p->dirty = true;
+    drop_pool_graphs(p);
+    return size_grid(p);
+}
+
+slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise) {
+    if (!p) return perr(SLBM_EINVAL, "null pool");
+    if (raise) {
+        *(volatile int32_t *)p->h_abort = 1;
+    } else {
+        const cudaError_t e = cudaStreamSynchronize(p->stream);
+        *(volatile int32_t *)p->h_abort = 0;
+        if (e == cudaSuccess) {
+            const cudaError_t e2 = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), p->stream);
+            if (e2 != cudaSuccess) return pcuda(e2, "pool abort clear");
+        } else {
+            return pcuda(e, "pool abort clear");
+        }
+    }
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+void slbm_pool_free(slbm_pool_t *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    drop_pool_graphs(p);
+    if (p->d_tab) cudaFree(p->d_tab);
+    if (p->d_hdr) cudaFree(p->d_hdr);
+    if (p->d_status) cudaFree(p->d_status);
+    if (p->d_red) cudaFree(p->d_red);
+    for (int v = 0; v < 2; ++v)
+        if (p->d_tiles[v]) cudaFree(p->d_tiles[v]);
+    if (p->d_begin) cudaFree(p->d_begin);
+    if (p->h_abort) cudaFreeHost(p->h_abort);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    cudaGetLastError();
+    delete p;
+}
+
+}  // extern "C"

@@ -128,8 +128,10 @@ class Domain:
         fn = A.lib().sparse_lbm_step_graph if graph else A.lib().sparse_lbm_step
         A.check(fn(self.h, int(n)))
 
-    def set_launch(self, parity: int, threads: int, cells: int):
-        A.check(A.lib().sparse_lbm_set_launch(self.h, parity, threads, cells))
+    def set_launch(self, parity: int, threads: int, cells: int, variant: int = 0):
+        """variant 0: `cells` consecutive cells per thread; variant 1: persistent
+        CTAs of `threads`-cell tiles with `cells` bulk-staged tiles in flight."""
+        A.check(A.lib().sparse_lbm_set_launch(self.h, parity, threads, cells, variant))
 
     def set_checked(self, on: bool):
         A.check(A.lib().sparse_lbm_set_checked(self.h, int(bool(on))))

@@ -1,0 +1,273 @@
+"""Continuous-batching server for permeability solves.
+
+Requests (voxel geometries with a body force) arrive over time.  The server
+admits a request as soon as a pool slot and enough HBM budget are free, keeps
+its PDF-list and index-list resident, steps every admitted request together
+(one persistent kernel launch per time step through `Pool`, CUDA-graph replay
+of `chunk` steps), checks each request's convergence after every chunk from
+its FP64 domain sums, and retires it -- freeing its slot and memory for the
+next arrival -- when the relative change of its mean fluid velocity over the
+last chunk drops below `tol`, or at `max_steps`.  A request whose sums stop
+being finite, or whose mean speed exceeds the stability bound, is retired
+with an error while the others keep running.
+
+The loop talks to an executor (`GpuExecutor` here; tests use a CPU fake with
+the same interface), so admission, batching and retirement are host logic
+independent of the device.  Permeability (lattice units^2) of a body-force
+driven periodic sample: k = nu * U_D / F_x with U_D = sum_fluid u_x / N.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _capi as A
+
+U_MAX_STABLE = 0.3
+
+
+@dataclass
+class Request:
+    rid: int
+    flags: np.ndarray
+    periodic: int = 7
+    force: tuple = (1e-6, 0.0, 0.0)
+    omega: float = 1.0 / 0.8
+    trt_magic: float = 3.0 / 16.0
+    arrival: float = 0.0                 # seconds after the start of the run
+    max_steps: int = 20000
+    tol: float = 1e-6
+    meta: dict = field(default_factory=dict)
+
+
+@dataclass
+class Result:
+    rid: int
+    permeability: float | None
+    steps: int
+    converged: bool
+    t_arrival: float
+    t_admit: float | None
+    t_finish: float
+    error: str | None = None
+    mean_ux: float | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_finish - self.t_arrival
+
+
+def nu_of(omega: float) -> float:
+    return (1.0 / omega - 0.5) / 3.0
+
+
+class GpuExecutor:
+    """Pool-backed executor: one `Domain` per admitted request, all stepped by
+    one `Pool`."""
+
+    def __init__(self, q: int = 19, storage: int = A.FP32, capacity: int = 64, scale_exp: int | None = None,
+                 graph: bool = True, stream=None, pool_launch: tuple | None = None):
+        from .domain import Domain, auto_scale_exp
+        from .pool import Pool
+        self._Domain = Domain
+        self.q, self.storage, self.graph = q, storage, graph
+        self.scale_exp = auto_scale_exp(1e-3) if scale_exp is None else scale_exp
+        self.stream = stream
+        self.pool = Pool(q, storage, capacity, stream=stream)
+        if pool_launch:
+            self.pool.set_launch(*pool_launch)
+        self.capacity = capacity
+
+    def footprint(self, req: Request) -> int:
+        """Device bytes a request will hold (PDF-list, index-list, cell list,
+        reduction partials), from its fluid-cell count."""
+        nf = int(np.count_nonzero(req.flags == 0))
+        S = (nf + 127) // 128 * 128
+        b = 4 if self.storage == A.FP32 else 2
+        return self.q * S * b + (self.q - 1) * S * 4 + nf * 4 + ((nf + 2047) // 2048) * 40 + 1024
+
+    def open(self, req: Request):
+        return self._Domain(req.flags, periodic=req.periodic, q=self.q, op=A.TRT, omega=req.omega,
+                            trt_magic=req.trt_magic, force=req.force, storage=self.storage,
+                            scale_exp=self.scale_exp, stream=self.stream)
+
+    def add(self, dom) -> int:
+        return self.pool.add(dom)
+
+    def remove(self, slot: int, dom) -> None:
+        self.pool.remove(slot)
+        dom.close()
+
+    def step(self, k: int) -> None:
+        self.pool.step(k, graph=self.graph)
+
+    def sums(self) -> np.ndarray:
+        return self.pool.reduce()
+
+    def close(self) -> None:
+        self.pool.close()
+
+
+class Server:
+    """Continuous batching over an executor.  `run()` serves a list of
+    requests with given arrival times and returns their results plus run
+    statistics (solves/s, p50/p99 latency)."""
+
+    def __init__(self, executor, budget_bytes: int, chunk: int = 100, lookahead: int = 8,
+                 clock=time.perf_counter, sleep=time.sleep, fault_hook=None):
+        if chunk <= 0 or chunk % 2:
+            raise ValueError("chunk must be a positive even number of steps")
+        self.ex = executor
+        self.budget = int(budget_bytes)
+        self.chunk = chunk
+        self.lookahead = lookahead
+        self.clock = clock
+        self.sleep = sleep
+        self.fault_hook = fault_hook      # tests: called as hook(event, rid) -> raise to inject
+
+    def run(self, requests: list[Request], realtime: bool = True) -> tuple[list[Result], dict]:
+        queue = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        t0 = self.clock()
+        active: dict[int, dict] = {}      # slot -> state
+        results: list[Result] = []
+        used = 0
+        busy_s = 0.0
+        updates = 0
+        while queue or active:
+            now = self.clock() - t0
+            # ---- admission: FIFO with bounded lookahead, by slot and budget
+            admitted_any = False
+            i = 0
+            while i < min(len(queue), self.lookahead) and len(active) < self.ex.capacity:
+                req = queue[i]
+                if realtime and req.arrival > now:
+                    break
+                need = self.ex.footprint(req)
+                if need > self.budget:
+                    queue.pop(i)
+                    results.append(Result(req.rid, None, 0, False, req.arrival, None, self.clock() - t0,
+                                          error="footprint exceeds the whole HBM budget"))
+                    continue
+                if used + need > self.budget:
+                    i += 1
+                    continue
+                queue.pop(i)
+                try:
+                    if self.fault_hook:
+                        self.fault_hook("open", req.rid)
+                    dom = self.ex.open(req)
+                    slot = self.ex.add(dom)
+                except Exception as e:  # creation failure: report, keep serving
+                    results.append(Result(req.rid, None, 0, False, req.arrival, None, self.clock() - t0,
+                                          error=f"open failed: {e}"))
+                    continue
+                active[slot] = dict(req=req, dom=dom, need=need, steps=0, prev=None,
+                                    t_admit=self.clock() - t0, n=int(req.flags.size),
+                                    nf=int(np.count_nonzero(req.flags == 0)))
+                used += need
+                admitted_any = True
+            if not active:
+                if queue and realtime:
+                    wait = queue[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(min(wait, 0.05))
+                continue
+            # ---- one chunk of steps for every active request
+            tb = self.clock()
+            try:
+                if self.fault_hook:
+                    self.fault_hook("step", None)
+                self.ex.step(self.chunk)
+                sums = self.ex.sums()
+            except A.SlbmError as e:
+                # a device-level failure ends every active request
+                for slot, st in list(active.items()):
+                    results.append(self._retire(slot, st, t0, error=f"step failed: {e}"))
+                    used -= st["need"]
+                active.clear()
+                continue
+            busy_s += self.clock() - tb
+            for slot, st in list(active.items()):
+                st["steps"] += self.chunk
+                updates += st["nf"] * self.chunk
+                s = sums[slot]
+                req = st["req"]
+                err = None
+                mean_ux = s[4] / max(st["nf"], 1)
+                if not np.all(np.isfinite(s)):
+                    err = "diverged: domain sums are not finite"
+                elif abs(mean_ux) > U_MAX_STABLE:
+                    err = "diverged: mean speed above the stability bound"
+                if self.fault_hook:
+                    try:
+                        self.fault_hook("check", req.rid)
+                    except Exception as e:
+                        err = f"injected: {e}"
+                done = err is not None
+                conv = False
+                if not done:
+                    prev = st["prev"]
+                    if prev is not None and mean_ux != 0.0 and abs(mean_ux - prev) / abs(mean_ux) < req.tol:
+                        done = conv = True
+                    elif st["steps"] >= req.max_steps:
+                        done = True
+                    st["prev"] = mean_ux
+                if done:
+                    results.append(self._retire(slot, st, t0, error=err, converged=conv, sums=s))
+                    used -= st["need"]
+                    del active[slot]
+        wall = self.clock() - t0
+        return results, self.stats(results, wall, busy_s, updates)
+
+    def _retire(self, slot, st, t0, error=None, converged=False, sums=None):
+        req = st["req"]
+        k = mean_ux = None
+        if error is None and sums is not None:
+            mean_ux = sums[4] / max(st["nf"], 1)
+            k = nu_of(req.omega) * (sums[4] / st["n"]) / req.force[0] if req.force[0] else None
+        try:
+            self.ex.remove(slot, st["dom"])
+        except Exception:
+            pass
+        return Result(req.rid, k, st["steps"], converged, req.arrival, st["t_admit"], self.clock() - t0,
+                      error=error, mean_ux=mean_ux)
+
+    @staticmethod
+    def stats(results: list[Result], wall: float, busy_s: float = 0.0, updates: int = 0) -> dict:
+        ok = [r for r in results if r.error is None]
+        lat = np.array([r.latency for r in ok]) if ok else np.array([math.nan])
+        return {"requests": len(results), "solved": len(ok), "failed": len(results) - len(ok),
+                "wall_s": wall, "solves_per_s": len(ok) / wall if wall > 0 else math.nan,
+                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "mflups": updates / wall / 1e6 if wall > 0 else math.nan, "device_busy_s": busy_s,
+                "converged": sum(r.converged for r in ok)}
+
+
+def solve_alone(req: Request, q: int = 19, storage: int = A.FP32, chunk: int = 100, graph: bool = True,
+                scale_exp: int | None = None, stream=None) -> Result:
+    """One request on its own (no pool): the one-at-a-time baseline, with the
+    same convergence test and the same kernels as the server."""
+    from .domain import Domain, auto_scale_exp
+    se = auto_scale_exp(1e-3) if scale_exp is None else scale_exp
+    t0 = time.perf_counter()
+    d = Domain(req.flags, periodic=req.periodic, q=q, op=A.TRT, omega=req.omega, trt_magic=req.trt_magic,
+               force=req.force, storage=storage, scale_exp=se, stream=stream)
+    n, nf = int(req.flags.size), d.n_fluid
+    prev, steps, conv, s = None, 0, False, None
+    try:
+        while steps < req.max_steps:
+            d.step(chunk, graph=graph)
+            steps += chunk
+            s = d.reduce()
+            m = s[4] / max(nf, 1)
+            if prev is not None and m != 0.0 and abs(m - prev) / abs(m) < req.tol:
+                conv = True
+                break
+            prev = m
+    finally:
+        d.close()
+    k = nu_of(req.omega) * (s[4] / n) / req.force[0]
+    return Result(req.rid, k, steps, conv, 0.0, 0.0, time.perf_counter() - t0, mean_ux=s[4] / max(nf, 1))

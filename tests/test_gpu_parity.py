@@ -156,19 +156,30 @@ def test_reductions_match_fields_and_are_deterministic():
     assert abs(s1[0]) < 1e-6
 
 
-@pytest.mark.parametrize("shape", [(64, 1), (128, 1), (256, 1), (64, 2), (256, 2), (128, 4), (256, 4)])
-def test_launch_shapes_are_bitwise_identical(shape):
-    g = G.boolean_spheres(40, 0.5, 9)    # N_F not a multiple of any tile
-    kw = dict(q=19, op=P.TRT, force=(1e-5, 2e-6, 0.0))
+SHAPES = [(64, 1, 0), (128, 1, 0), (256, 1, 0), (64, 2, 0), (256, 2, 0), (128, 4, 0), (256, 4, 0),
+          (64, 2, 1), (64, 4, 1), (128, 2, 1), (128, 4, 1)]
+
+
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16])
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_launch_shapes_are_bitwise_identical(shape, q, storage):
+    # every launch shape, including the bulk-staged persistent kernels, gives
+    # the same bits; mixed inlet/outlet links exercise the link maps too
+    g = _mixed_bc(13, (40, 33, 29)) if q == 27 else G.boolean_spheres(40, 0.5, 9)
+    kw = dict(q=q, op=P.TRT, force=(1e-5, 2e-6, 0.0), storage=storage, scale_exp=20)
     with gpu_domain(g, **kw) as ref:
-        ref.step(6)
+        ref.set_launch(0, 128, 1)
+        ref.set_launch(1, 128, 1)
+        ref.step(7)
         want, _ = ref.get_state()
-    threads, cells = shape
+    threads, cells, variant = shape
     with gpu_domain(g, **kw) as d:
-        d.set_launch(0, threads, cells)
-        d.set_launch(1, threads, min(cells, 2))
-        d.step(6)
+        d.set_launch(0, threads, cells, variant)
+        d.set_launch(1, threads, cells if variant else min(cells, 2), variant)
+        d.step(7)
         got, _ = d.get_state()
+        assert d.device_error() == 0
     assert np.array_equal(got, want)
 
 
