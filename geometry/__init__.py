@@ -251,10 +251,14 @@ def _tree_segments(seed: int, depth: int, r0: float, r_leaf: float, lam: float, 
     return segs
 
 
-def _stamp_segments(shape, segs, cap_value=None):
-    nx, ny, nz = shape
+def _stamp_segments(shape, segs, coarse=1):
+    """Voxels whose centre lies within r of a segment (capsules).  With
+    coarse = c > 1 the box is sampled at every c-th voxel centre."""
+    nx, ny, nz = (-(-n // coarse) for n in shape)
     inside = np.zeros((nz, ny, nx), bool)
     for p0, p1, r, _ in segs:
+        if coarse > 1:
+            p0, p1, r = (p0 - (coarse - 1) / 2.0) / coarse, (p1 - (coarse - 1) / 2.0) / coarse, r / coarse
         lo = np.maximum(np.floor(np.minimum(p0, p1) - r).astype(int), 0)
         hi = np.minimum(np.ceil(np.maximum(p0, p1) + r).astype(int), [nx - 1, ny - 1, nz - 1])
         if np.any(hi < lo):
@@ -288,15 +292,15 @@ def artery_tree(nx: int = 1024, ny: int = 512, nz: int = 512, depth: int = 6,
     is wall."""
     start = (0.0, ny / 2.0, nz / 2.0)
 
-    def build(l):
+    def build(l, coarse=1):
         segs = _tree_segments(seed, depth, r0, r_leaf, l, start)
-        return segs, _stamp_segments((nx, ny, nz), segs)
+        return segs, _stamp_segments((nx, ny, nz), segs, coarse)
 
-    if lam is None:
+    if lam is None:     # bisection on a 4x coarser sampling of the box
         lo, hi = 1.0, 40.0
         for _ in range(12):
             mid = 0.5 * (lo + hi)
-            _, ins = build(mid)
+            _, ins = build(mid, 4)
             if ins.mean() < target_fluid:
                 lo = mid
             else:

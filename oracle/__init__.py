@@ -83,6 +83,7 @@ def lib():
             L.orc_pull_list.argtypes = [P, vp, vp, i64, i64, vp, vp, vp, vp, vp, i64]
             L.orc_pull_list.restype = i64
             L.orc_sparse_run.argtypes = [P, vp, i64, i64, vp, vp, vp, C.c_int]
+            L.orc_sparse_macroscopic.argtypes = [P, vp, i64, i64, vp, vp]
             L.orc_max_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -279,6 +280,24 @@ def sparse_run(p: Problem, lists: Lists, f: np.ndarray, steps: int) -> np.ndarra
                             _ptr(bu), _ptr(f), int(steps)) != 0:
         raise MemoryError("oracle sparse_run")
     return f
+
+
+def sparse_rest(p: Problem, lists: Lists) -> np.ndarray:
+    """The rest state on a PDF-list: f_i = w_i (the equilibrium at rho = 1,
+    u = 0) in every fluid column, zero padding."""
+    _, w, _ = stencil(p.q)
+    f = np.zeros((p.q, lists.stride))
+    f[:, :lists.n_fluid] = w[:, None]
+    return f
+
+
+def sparse_macroscopic(p: Problem, lists: Lists, f: np.ndarray):
+    """(rho[N_F], u[N_F,3]) of a PDF-list, Guo half-force velocity (Eq. 1)."""
+    nf = lists.n_fluid
+    rho = np.zeros(max(nf, 1))
+    u = np.zeros((max(nf, 1), 3))
+    lib().orc_sparse_macroscopic(p._c(), _ptr(np.ascontiguousarray(f)), nf, lists.stride, _ptr(rho), _ptr(u))
+    return rho[:nf], u[:nf]
 
 
 # ------------------------------------------------------- derived quantities

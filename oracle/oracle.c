@@ -279,6 +279,16 @@ void orc_dense_macroscopic(const orc_problem *p, const double *f, double *rho, d
     }
 }
 
+/* rho, u (Guo-corrected) of every cell of a PDF-list (Q x S, slot i*S + k). */
+void orc_sparse_macroscopic(const orc_problem *p, const double *f, int64_t nf, int64_t S, double *rho, double *u) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nf; ++k) {
+        double fl[27];
+        for (int i = 0; i < p->q; ++i) fl[i] = f[(int64_t)i * S + k];
+        orc_moments(p->q, fl, p->force, &rho[k], &u[3 * k]);
+    }
+}
+
 /* ------------------------------------------------------- sparse indexing */
 
 /* Compacted fluid-cell order (Sec. 3.1): fluid voxels numbered in

@@ -1,0 +1,138 @@
+"""Parity on each workload, at full size in the launch configuration the
+benchmark uses (default launch shapes), and at reduced size for the full step
+counts.  The oracle side is the FP64 sparse pull stepper on the oracle's own
+lists (pinned bit for bit to its dense stepper in test_oracle_lists.py); at
+full size it runs a short number of steps, since the domain of dependence of
+a long run is the whole box.
+
+Workloads: the 256^3 porosity sweep (D3Q19 TRT), the 512 x 256 x 256 particle
+bed with inlet and outlet (D3Q27 TRT), the 1024 x 512 x 512 artery tree
+(D3Q19 TRT, inlet/outlet), and requests of the permeability stream solved to
+convergence."""
+import numpy as np
+import pytest
+
+import geometry as G
+import oracle as O
+from helpers import gpu_domain, rel_l2
+
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_2408_06880_gb300")
+
+U_TOL = 1e-5
+TRT = dict(op=P.TRT, omega=1.25, trt_magic=3 / 16)
+
+
+def oracle_cells(g, steps, q, force, lists=None):
+    p = O.Problem.from_geometry(g, q=q, op=O.TRT, omega_plus=1.25, magic=3 / 16, force=force)
+    L = lists or O.pull_list(p)
+    f = O.sparse_run(p, L, O.sparse_rest(p, L), steps)
+    rho, u = O.sparse_macroscopic(p, L, f)
+    return L, rho, u
+
+
+def gpu_cells(g, steps, q, force, **kw):
+    with gpu_domain(g, q=q, force=force, **TRT, **kw) as d:
+        lists = d.export_lists()
+        d.step(steps)
+        rho, u = d.macroscopic(P.ORDER_CELLS)
+    return lists, rho.astype(np.float64), u.T.astype(np.float64)
+
+
+def assert_lists_equal(got, ref):
+    assert got["n_fluid"] == ref.n_fluid and got["stride"] == ref.stride
+    assert np.array_equal(got["cell_voxel"], ref.cell_voxel)
+    assert np.array_equal(got["P"], ref.P)
+    assert np.array_equal(got["link_cell"], ref.bc_cell)
+    assert np.array_equal(got["link_dir"], ref.bc_dir)
+    assert np.array_equal(got["link_type"], ref.bc_type)
+
+
+def assert_fields_close(rho, u, rho_o, u_o):
+    assert rel_l2(u, u_o) <= U_TOL, rel_l2(u, u_o)
+    assert np.max(np.abs(rho - rho_o)) <= 1e-6
+
+
+# ------------------------------------------------------- 256^3 porosity sweep
+@pytest.mark.parametrize("phi,seed", [(0.3, 11), (0.9, 14)])
+def test_sweep_full_size(phi, seed):
+    g = G.boolean_spheres(256, phi, seed)
+    force = (1e-6, 0.0, 0.0)
+    lists, rho, u = gpu_cells(g, 20, 19, force)
+    L, rho_o, u_o = oracle_cells(g, 20, 19, force)
+    assert_lists_equal(lists, L)
+    assert_fields_close(rho, u, rho_o, u_o)
+
+
+def test_sweep_scaled_full_step_count():
+    g = G.boolean_spheres(64, 0.5, 12)
+    force = (1e-6, 0.0, 0.0)
+    _, rho, u = gpu_cells(g, 1000, 19, force)
+    _, rho_o, u_o = oracle_cells(g, 1000, 19, force)
+    assert_fields_close(rho, u, rho_o, u_o)
+
+
+def test_sweep_full_size_mass_and_momentum_balance():
+    # properties that hold at any size: periodic box with bounce-back keeps
+    # the mass; after 1000 steps of forcing the flow is along +x
+    g = G.boolean_spheres(256, 0.5, 12)
+    with gpu_domain(g, q=19, force=(1e-6, 0.0, 0.0), **TRT) as d:
+        d.step(1000)
+        s = d.reduce()
+        nf = d.n_fluid
+    assert abs(s[0]) < 1e-6 * nf ** 0.5
+    assert s[1] > 0 and abs(s[2]) < 1e-3 * s[1] and abs(s[3]) < 1e-3 * s[1]
+
+
+# -------------------------------------------------------------- particle bed
+def test_bed_full_size():
+    g = G.particle_bed()
+    lists, rho, u = gpu_cells(g, 6, 27, (0.0, 0.0, 0.0))
+    L, rho_o, u_o = oracle_cells(g, 6, 27, (0.0, 0.0, 0.0))
+    assert lists["link_cell"].size > 0
+    assert_lists_equal(lists, L)
+    assert_fields_close(rho, u, rho_o, u_o)
+
+
+def test_bed_scaled_full_step_count_fp32_and_fp16():
+    g = G.particle_bed(64, 32, 32, bed_top=16, radius=4.0, seed=22)
+    _, rho, u = gpu_cells(g, 5000, 27, (0.0, 0.0, 0.0))
+    _, rho_o, u_o = oracle_cells(g, 5000, 27, (0.0, 0.0, 0.0))
+    assert_fields_close(rho, u, rho_o, u_o)
+    # FP16 shifted storage (scale chosen for |u| ~ 0.05): stated error
+    _, rho16, u16 = gpu_cells(g, 5000, 27, (0.0, 0.0, 0.0), storage=P.FP16,
+                              scale_exp=P.auto_scale_exp(0.06, 0.01))
+    assert rel_l2(u16, u_o) <= 5e-3
+
+
+# --------------------------------------------------------------- artery tree
+def test_artery_full_size():
+    g = G.artery_tree()
+    assert g.meta["fluid_fraction"] > 0.004
+    lists, rho, u = gpu_cells(g, 10, 19, (0.0, 0.0, 0.0))
+    L, rho_o, u_o = oracle_cells(g, 10, 19, (0.0, 0.0, 0.0))
+    assert_lists_equal(lists, L)
+    assert_fields_close(rho, u, rho_o, u_o)
+
+
+def test_artery_scaled_full_step_count():
+    g = G.artery_tree(256, 128, 128, r0=5.0, r_leaf=1.0)
+    _, rho, u = gpu_cells(g, 2000, 19, (0.0, 0.0, 0.0))
+    _, rho_o, u_o = oracle_cells(g, 2000, 19, (0.0, 0.0, 0.0))
+    assert_fields_close(rho, u, rho_o, u_o)
+
+
+# ------------------------------------------------------- permeability stream
+@pytest.mark.parametrize("rid", [14, 7])
+def test_stream_request_permeability_matches_oracle(rid):
+    from paper_2408_06880_gb300.serving import Request, solve_alone
+    g = G.serving_request(rid)
+    req = Request(rid, g.flags, force=(1e-6, 0.0, 0.0), max_steps=20000, tol=1e-6)
+    r = solve_alone(req, storage=P.FP32)
+    assert r.converged
+    p = O.Problem.from_geometry(g, q=19, op=O.TRT, omega_plus=1.25, magic=3 / 16, force=(1e-6, 0.0, 0.0))
+    L = O.pull_list(p)
+    f = O.sparse_run(p, L, O.sparse_rest(p, L), r.steps)
+    _, u = O.sparse_macroscopic(p, L, f)
+    k_oracle = O.permeability(p, float(np.sum(u[:, 0])))
+    assert abs(r.permeability / k_oracle - 1) <= 1e-5

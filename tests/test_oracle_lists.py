@@ -157,3 +157,14 @@ def test_sparse_equals_dense_bitwise(q, name, make, op):
     want = fd[:, L.cell_voxel]
     assert np.array_equal(got, want)          # bit for bit
     assert not np.array_equal(want, f0[:, L.cell_voxel])
+    # the PDF-list readout equals the dense readout on the fluid voxels
+    rs, us = O.sparse_macroscopic(p, L, fs)
+    rd, ud = O.dense_macroscopic(p, fd)
+    assert np.array_equal(rs, rd[L.cell_voxel]) and np.array_equal(us, ud[L.cell_voxel])
+
+
+def test_sparse_rest_state_is_the_dense_rest_state():
+    g = G.random_solids(6, 0.3, 4)
+    p = O.Problem.from_geometry(g, q=27)
+    L = O.pull_list(p)
+    assert np.array_equal(O.sparse_rest(p, L), O.sparse_from_dense(L, O.dense_init(p)))
