@@ -277,7 +277,7 @@ def _stamp_segments(shape, segs, coarse=1):
 
 
 def artery_tree(nx: int = 1024, ny: int = 512, nz: int = 512, depth: int = 6,
-                r0: float = 20.0, r_leaf: float = 4.0, u_max: float = 0.05,
+                r0: float = 20.0, r_leaf: float = 4.0, u_max: float = 0.01,
                 target_fluid: float = 0.03, seed: int = 31, lam: float | None = None) -> Geometry:
     """Synthetic coronary-like tree (stand-in for Sec. 6.3).
 

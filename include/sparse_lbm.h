@@ -171,7 +171,10 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
  * variant 1: persistent CTAs (SMs x resident CTAs) that walk tiles of
  *            `threads` cells (64 or 128) and keep `cells` tiles (2 or 4) of
  *            index-list rows (odd) or PDF rows (even) in flight in shared
- *            memory through asynchronous bulk copies; sparse FP32/FP16 only.
+ *            memory through asynchronous bulk copies; sparse FP32/FP16 only;
+ * variant 2: odd step only, as variant 0 with 1 cell per thread, plus an
+ *            asynchronous bulk L2 prefetch of the index-list rows of the block
+ *            that will run one residency wave later.
  * Defaults: variant 0, 64 x 2 (even; FP16: variant 1, 128 x 2) and 64 x 1
  * (odd).  Results are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);

@@ -17,9 +17,9 @@
  *   - stream   f_i(x + c_i, t+1) = f~_i(x, t)                             (Eq. 4)
  *     as a two-grid PUSH over a dense, direct-addressed box (Sec. 3),
  *     with halfway bounce-back at walls (Sec. 3.1.1), periodic wrap,
- *     a Ladd moving-wall (UBB) inlet and a linearised anti-bounce-back
- *     pressure outlet (both textbook forms; the paper only says such
- *     boundaries exist, Sec. 3.1.1).
+ *     a Ladd moving-wall (UBB) inlet and an anti-bounce-back pressure outlet
+ *     whose equilibrium uses the boundary cell's own velocity (both textbook
+ *     forms; the paper only says such boundaries exist, Sec. 3.1.1).
  *   - its own sparse indexing (Sec. 3.1): the compacted fluid-cell order
  *     (lexicographic, x fastest), the pull index-list P(i,k) with no-slip
  *     links pointing at the same cell's inverse direction and periodic links
@@ -158,17 +158,25 @@ void orc_collide(const orc_problem *p, const double *f, double *fs) {
 
 /* Value a boundary link hands to the fluid cell: the PDF of direction r
  * that re-enters the cell after its own post-collision PDF of direction
- * inverse(r) (value `src`) hit the boundary voxel.
- *   wall:   src                              (halfway bounce-back)
- *   inlet:  src + 6 w_r rho0 (c_r . u_w)      (Ladd moving wall, rho0 = 1)
- *   outlet: -src + 2 w_r rho_out             (linearised anti-bounce-back) */
-static double bc_value(const orc_problem *p, int type, double src, int r, const double *uw) {
+ * inverse(r) (value `src`) hit the boundary voxel.  `uc` is the cell's own
+ * velocity (Eq. 1 with the Guo half force) at the collision that produced
+ * `src`.
+ *   wall:   src                                        (halfway bounce-back)
+ *   inlet:  src + 6 w_r rho0 (c_r . u_w), rho0 = 1      (Ladd moving wall)
+ *   outlet: -src + 2 w_r rho_out (1 + 4.5 (c_r . uc)^2 - 1.5 uc . uc)
+ *           (anti-bounce-back towards the even part of the equilibrium at the
+ *           outlet density and the cell's velocity) */
+static double bc_value(const orc_problem *p, int type, double src, int r, const double *uw, const double *uc) {
     double w = weight(p->q, r);
     if (type == ORC_INLET) {
         double cu = VEL[r][0] * uw[0] + VEL[r][1] * uw[1] + VEL[r][2] * uw[2];
         return src + 6.0 * w * cu;
     }
-    if (type == ORC_OUTLET) return -src + 2.0 * w * p->rho_out;
+    if (type == ORC_OUTLET) {
+        double cu = VEL[r][0] * uc[0] + VEL[r][1] * uc[1] + VEL[r][2] * uc[2];
+        double uu = uc[0] * uc[0] + uc[1] * uc[1] + uc[2] * uc[2];
+        return -src + 2.0 * w * p->rho_out * (1.0 + 4.5 * cu * cu - 1.5 * uu);
+    }
     return src;
 }
 
@@ -239,8 +247,9 @@ int orc_dense_run(const orc_problem *p, double *f, int steps) {
         for (int64_t v = 0; v < n; ++v) {
             if (p->flags[v] != ORC_FLUID) continue;
             int x = (int)(v % p->nx), y = (int)((v / p->nx) % p->ny), z = (int)(v / ((int64_t)p->nx * p->ny));
-            double fl[27], fs[27];
+            double fl[27], fs[27], rho, uc[3];
             for (int i = 0; i < q; ++i) fl[i] = A[(int64_t)i * n + v];
+            orc_moments(q, fl, p->force, &rho, uc);
             orc_collide(p, fl, fs);
             for (int i = 0; i < q; ++i) {
                 int64_t nb = neighbour(p, x, y, z, VEL[i][0], VEL[i][1], VEL[i][2]);
@@ -249,7 +258,7 @@ int orc_dense_run(const orc_problem *p, double *f, int steps) {
                     B[(int64_t)i * n + nb] = fs[i];
                 } else {
                     int r = inverse(q, i);
-                    B[(int64_t)r * n + v] = bc_value(p, ty, fs[i], r, inlet_velocity(p, rank, nb));
+                    B[(int64_t)r * n + v] = bc_value(p, ty, fs[i], r, inlet_velocity(p, rank, nb), uc);
                 }
             }
         }
@@ -360,20 +369,26 @@ int64_t orc_pull_list(const orc_problem *p, const int32_t *cell_id, const int32_
 /* ---------------------------------------------------- sparse stepping */
 
 /* Two-grid PULL stepping over the PDF-list (Q x S, slot i*S + k):
- * collide every cell into C, then f_i(k) <- C[P(i,k)] for fluid/wall
- * links and the boundary value of C[inverse(i)*S + k] for inlet/outlet
- * links.  Uses the same per-cell arithmetic as orc_dense_run, so the two
- * agree bit for bit. */
+ * collide every cell into C (keeping each cell's velocity), then
+ * f_i(k) <- C[P(i,k)] for fluid/wall links and the boundary value of
+ * C[inverse(i)*S + k] for inlet/outlet links.  Uses the same per-cell
+ * arithmetic as orc_dense_run, so the two agree bit for bit. */
 int orc_sparse_run(const orc_problem *p, const int32_t *P, int64_t nf, int64_t S,
                    const int32_t *bc_type, const double *bc_u, double *f, int steps) {
     int q = p->q;
     double *C = (double *)malloc(sizeof(double) * (size_t)(q * S > 0 ? q * S : 1));
-    if (!C) return -1;
+    double *U = (double *)malloc(sizeof(double) * (size_t)(3 * nf > 0 ? 3 * nf : 1));
+    if (!C || !U) {
+        free(C);
+        free(U);
+        return -1;
+    }
     for (int t = 0; t < steps; ++t) {
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < nf; ++k) {
-            double fl[27], fs[27];
+            double fl[27], fs[27], rho;
             for (int i = 0; i < q; ++i) fl[i] = f[(int64_t)i * S + k];
+            orc_moments(q, fl, p->force, &rho, &U[3 * k]);
             orc_collide(p, fl, fs);
             for (int i = 0; i < q; ++i) C[(int64_t)i * S + k] = fs[i];
         }
@@ -388,12 +403,13 @@ int orc_sparse_run(const orc_problem *p, const int32_t *P, int64_t nf, int64_t S
                     int64_t b = -(int64_t)e - 1;
                     int r = inverse(q, i);
                     f[(int64_t)i * S + k] =
-                        bc_value(p, bc_type[b], C[(int64_t)r * S + k], i, bc_u + 3 * b);
+                        bc_value(p, bc_type[b], C[(int64_t)r * S + k], i, bc_u + 3 * b, &U[3 * k]);
                 }
             }
         }
     }
     free(C);
+    free(U);
     return 0;
 }
 

@@ -17,10 +17,13 @@
 //     row i of column k: the bounced-back value), so the field is natural
 //     again.  Each slot is read and written by one cell only, hence in place
 //     without races.
-// Boundary links (inlet/outlet) keep the cell's own slot i*S + k and apply
-// their affine map on the read and on the write.
+// Boundary links (inlet/outlet) keep the cell's own slot i*S + k; the value
+// stored there is the link's map of the post-collision value, applied when it
+// is written (here for the odd step; around the even step by the boundary
+// fix-up kernels), so reads are plain.
 #pragma once
 
+#include "bulk.cuh"
 #include "common.cuh"
 
 namespace slbm {
@@ -101,13 +104,25 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
     if (err) atomicCAS(err, 0, code);
 }
 
+// pf_dist > 0 (CPT = 1 only): thread 0 first asks the bulk-copy engine to
+// prefetch into L2 the index-list rows of the CTA pf_dist blocks ahead -- about
+// one residency wave later -- so that CTA's first round trip hits L2.
 template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK>
 __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                      const int32_t *__restrict__ P, int32_t S, int32_t nf,
                                                      const LinkMap *__restrict__ maps, int32_t n_links,
-                                                     CollideParams p, int32_t *err) {
+                                                     CollideParams p, int32_t *err, int32_t pf_dist) {
     using St = Store<ST>;
     using T = typename St::T;
+    if (CPT == 1 && pf_dist > 0 && threadIdx.x == 0) {
+        const int64_t c0 = ((int64_t)blockIdx.x + pf_dist) * blockDim.x;
+        if (c0 < nf) {
+            const int64_t left = (int64_t)S - c0;
+            const uint32_t bytes = (uint32_t)(left < (int64_t)blockDim.x ? left : (int64_t)blockDim.x) * 4u;
+#pragma unroll
+            for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(P + r * S + c0, bytes);
+        }
+    }
     const int32_t k0 = (blockIdx.x * blockDim.x + threadIdx.x) * CPT;
     if (k0 >= nf) return;
     int32_t e[CPT][Q];
@@ -143,14 +158,11 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
             R[c][i] = r;
             if (valid) g[c][i] = St::raw(pdf[r]);
             else g[c][i] = 0.f;
-            if (HAS_BC && valid && ee < 0) {
-                const LinkMap m = maps[-(ee + 1)];
-                g[c][i] = m.s * g[c][i] + m.a * p.scale;
-            }
         }
     }
+    Vel u[CPT];
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+    for (int c = 0; c < CPT; ++c) u[c] = collide<Q, St::scaled>(g[c], p);
     {
         Vec<T, CPT> y;
 #pragma unroll
@@ -169,10 +181,7 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             float v = g[c][inv(i)];
-            if (HAS_BC && e[c][i] < 0) {
-                const LinkMap m = maps[-(e[c][i] + 1)];
-                v = m.s * v + m.a * p.scale;
-            }
+            if (HAS_BC && e[c][i] < 0) v = apply_link(maps[-(e[c][i] + 1)], v, u[c].x, u[c].y, u[c].z, p.scale);
             pdf[R[c][i]] = St::pack(v);
         }
     }
@@ -192,11 +201,50 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
 // the loop together, after the elected thread has waited (bounded) for the
 // copies it still has in flight.  TILE divides 128 and the row stride S is a
 // multiple of 128, so every tile is whole and every copy is 16-byte aligned.
-#include "bulk.cuh"
-
 namespace slbm {
 
 constexpr int32_t ERR_STAGE_TIMEOUT = 100;
+
+// ---------------------------------------------------------------------------
+// Boundary fix-up around the even step (domains with inlet/outlet links).
+// The even step stays cell-local and index-free; before it, each boundary
+// cell's velocity at the current time is saved; after it, the values the even
+// step stored in the cell's link slots are replaced by their link maps.
+template <int Q, int ST>
+__global__ void bc_pre_kernel(const typename Store<ST>::T *__restrict__ pdf, int32_t S,
+                              const int32_t *__restrict__ bcell, int32_t n_bcells, CollideParams p,
+                              float *__restrict__ ubuf) {
+    using St = Store<ST>;
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_bcells) return;
+    const int32_t k = bcell[j];
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = St::ld(pdf[i * S + k], p.inv_scale);
+    float drho, jx, jy, jz;
+    moments<Q>(g, drho, jx, jy, jz);
+    const float rho = 1.0f + drho;
+    ubuf[3 * j] = (jx + 0.5f * p.fx) / rho;
+    ubuf[3 * j + 1] = (jy + 0.5f * p.fy) / rho;
+    ubuf[3 * j + 2] = (jz + 0.5f * p.fz) / rho;
+}
+
+template <int ST>
+__global__ void bc_post_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S, const int32_t *__restrict__ bcell,
+                               const int32_t *__restrict__ bfirst, int32_t n_bcells,
+                               const int32_t *__restrict__ link_dir, const LinkMap *__restrict__ maps,
+                               const float *__restrict__ ubuf, float scale) {
+    using St = Store<ST>;
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_bcells) return;
+    const int32_t k = bcell[j];
+    const float ux = ubuf[3 * j], uy = ubuf[3 * j + 1], uz = ubuf[3 * j + 2];
+    for (int32_t b = bfirst[j]; b < bfirst[j + 1]; ++b) {
+        typename Store<ST>::T *slot = pdf + link_dir[b] * S + k;
+        *slot = St::pack(apply_link(maps[b], St::raw(*slot), ux, uy, uz, scale));
+    }
+}
+
 
 // The odd-step update of one cell from its Q-1 pull entries.
 template <int Q, int ST, bool HAS_BC>
@@ -212,20 +260,13 @@ __device__ __forceinline__ void odd_cell(typename Store<ST>::T *__restrict__ pdf
         const int32_t ee = e[i];
         R[i] = (HAS_BC && ee < 0) ? i * S + k : ee;
         g[i] = St::raw(pdf[R[i]]);
-        if (HAS_BC && ee < 0) {
-            const LinkMap m = maps[-(ee + 1)];
-            g[i] = m.s * g[i] + m.a * p.scale;
-        }
     }
-    collide<Q, St::scaled>(g, p);
+    const Vel u = collide<Q, St::scaled>(g, p);
     pdf[k] = St::pack(g[0]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         float v = g[inv(i)];
-        if (HAS_BC && e[i] < 0) {
-            const LinkMap m = maps[-(e[i] + 1)];
-            v = m.s * v + m.a * p.scale;
-        }
+        if (HAS_BC && e[i] < 0) v = apply_link(maps[-(e[i] + 1)], v, u.x, u.y, u.z, p.scale);
         pdf[R[i]] = St::pack(v);
     }
 }

@@ -56,13 +56,48 @@ static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Boundary fix-up launches around the even step of a domain with links.
+template <int Q, int ST>
+cudaError_t launch_bc_pre(const Domain &d, cudaStream_t st) {
+    const int32_t nb = (int32_t)d.n_bcells;
+    if (nb == 0) return cudaSuccess;
+    bc_pre_kernel<Q, ST><<<(nb + 127) / 128, 128, 0, st>>>(reinterpret_cast<const typename Store<ST>::T *>(d.pdf.p),
+                                                           (int32_t)d.S, (const int32_t *)d.bcell.p, nb,
+                                                           d.collide_params(), (float *)d.bc_ubuf.p);
+    return cudaGetLastError();
+}
+
+template <int Q, int ST>
+cudaError_t launch_bc_post(const Domain &d, cudaStream_t st) {
+    const int32_t nb = (int32_t)d.n_bcells;
+    if (nb == 0) return cudaSuccess;
+    bc_post_kernel<ST><<<(nb + 127) / 128, 128, 0, st>>>(
+        reinterpret_cast<typename Store<ST>::T *>(d.pdf.p), (int32_t)d.S, (const int32_t *)d.bcell.p,
+        (const int32_t *)d.bfirst.p, nb, (const int32_t *)d.link_dir.p, (const LinkMap *)d.link_map.p,
+        (const float *)d.bc_ubuf.p, d.collide_params().scale);
+    return cudaGetLastError();
+}
+
+template <int Q, int ST>
+static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st);
+
 template <int Q, int ST>
 static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
+    if (parity != 0 || d.n_bcells == 0) return launch_aa_storage_core<Q, ST>(d, parity, st);
+    cudaError_t e = launch_bc_pre<Q, ST>(d, st);
+    if (e == cudaSuccess) e = launch_aa_storage_core<Q, ST>(d, parity, st);
+    if (e == cudaSuccess) e = launch_bc_post<Q, ST>(d, st);
+    return e;
+}
+
+template <int Q, int ST>
+static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
     const LaunchShape sh = d.shape[parity];
+    if (sh.variant == 2 && parity == 0) return cudaErrorInvalidValue;
     if (sh.variant == 1 && !d.checked && ST != ST_BF16) {
         switch (sh.threads * 10 + sh.cells) {
             case 642: return launch_staged<Q, ST, 64, 2>(d, parity, st);
@@ -89,18 +124,34 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const bool bc = nl > 0;
     if (d.checked) {
-        if (bc) aa_odd_kernel<Q, ST, 1, true, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err);
-        else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err);
+        if (bc) aa_odd_kernel<Q, ST, 1, true, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0);
+        else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0);
         return cudaGetLastError();
     }
+    // variant 2: L2 prefetch of the index rows one residency wave ahead
+    int32_t pf = 0;
+    if (sh.variant == 2 && sh.cells == 1) {
+        auto kp = bc ? aa_odd_kernel<Q, ST, 1, true, false> : aa_odd_kernel<Q, ST, 1, false, false>;
+        pf = (int32_t)persistent_grid(kp, sh.threads, INT32_MAX);
+    }
     switch (sh.cells * 2 + (bc ? 1 : 0)) {
-        case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
-        case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
-        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
-        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err); break;
+        case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
+        case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
+        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0); break;
+        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Fix-ups for the pool's even step (per member with links).
+template <int Q>
+cudaError_t launch_bc_fixup_q(const Domain &d, int post, cudaStream_t st) {
+    switch (d.storage) {
+        case SLBM_FP32: return post ? launch_bc_post<Q, ST_F32>(d, st) : launch_bc_pre<Q, ST_F32>(d, st);
+        case SLBM_FP16: return post ? launch_bc_post<Q, ST_F16>(d, st) : launch_bc_pre<Q, ST_F16>(d, st);
+        default: return post ? launch_bc_post<Q, ST_BF16>(d, st) : launch_bc_pre<Q, ST_BF16>(d, st);
+    }
 }
 
 template <int Q>

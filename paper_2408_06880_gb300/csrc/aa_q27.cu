@@ -2,4 +2,5 @@
 #include "aa_launch.cuh"
 namespace slbm {
 template cudaError_t launch_aa_step_q<27>(const Domain &, int, cudaStream_t);
+template cudaError_t launch_bc_fixup_q<27>(const Domain &, int, cudaStream_t);
 }

@@ -103,6 +103,15 @@ cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st) {
     return d.q == 19 ? launch_aa_step_q<19>(d, parity, st) : launch_aa_step_q<27>(d, parity, st);
 }
 
+template <int Q>
+cudaError_t launch_bc_fixup_q(const Domain &d, int post, cudaStream_t st);
+extern template cudaError_t launch_bc_fixup_q<19>(const Domain &, int, cudaStream_t);
+extern template cudaError_t launch_bc_fixup_q<27>(const Domain &, int, cudaStream_t);
+
+cudaError_t launch_bc_fixup(const Domain &d, int post, cudaStream_t st) {
+    return d.q == 19 ? launch_bc_fixup_q<19>(d, post, st) : launch_bc_fixup_q<27>(d, post, st);
+}
+
 static cudaError_t launch_one_step(const Domain &d, int parity, cudaStream_t st) {
     return d.layout == SLBM_LAYOUT_SPARSE ? launch_aa_step(d, parity, st) : launch_dense_step(d, parity, st);
 }
@@ -114,8 +123,9 @@ static void drop_graphs(Domain &d) {
 
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
-    DevBuf *bufs[] = {&d.pdf, &d.P, &d.cell_voxel, &d.link_cell, &d.link_dir, &d.link_type, &d.link_map,
-                      &d.mask, &d.red_partial, &d.red_out, &d.err};
+    DevBuf *bufs[] = {&d.pdf,  &d.P,      &d.cell_voxel, &d.link_cell,   &d.link_dir, &d.link_type,
+                      &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask, &d.red_partial,
+                      &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
 }
 
@@ -469,8 +479,11 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variant covers sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
+    } else if (variant == 2) {
+        if (parity != 1 || cells != 1 || threads < 32 || threads > 256 || threads % 32)
+            return err(SLBM_EINVAL, "variant 2 is for the odd step: threads 32..256 (multiple of 32), cells 1");
     } else {
-        return err(SLBM_EINVAL, "variant must be 0 or 1");
+        return err(SLBM_EINVAL, "variant must be 0, 1 or 2");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);

@@ -95,13 +95,23 @@ struct CollideParams {
     float kappa[MAX_PAIRS];
 };
 
-// Boundary link map applied to a slot on both its read and its write in the
-// odd step: value -> s * value + a (shifted, unscaled units).
-//   velocity inlet (moving wall):  s =  1, a = 6 w_i (c_i . u_w)
-//   pressure outlet (anti-BB):     s = -1, a = 2 w_i (rho_out - 1)
+// Boundary link of cell k, direction i (the pull neighbour x_k - c_i is an
+// inlet or outlet voxel).  When the cell's post-collision value of direction
+// inverse(i) is stored into the link's slot i*S + k, it is mapped (shifted,
+// unscaled units, u = the cell's velocity at that collision):
+//   value -> s * value + a + q2 (4.5 (c_i . u)^2 - 1.5 u . u)
+//   velocity inlet (moving wall):  s =  1, a = 6 w_i (c_i . u_w),      q2 = 0
+//   pressure outlet (anti-BB):     s = -1, a = 2 w_i (rho_out - 1),    q2 = 2 w_i rho_out
 struct LinkMap {
-    float s, a;
+    float s, a, q2;
+    float cx, cy, cz;   // c_i
 };
+
+__device__ __forceinline__ float apply_link(const LinkMap &m, float v, float ux, float uy, float uz, float scale) {
+    const float cu = m.cx * ux + m.cy * uy + m.cz * uz;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    return m.s * v + scale * (m.a + m.q2 * (4.5f * cu * cu - 1.5f * uu));
+}
 
 // Moments of shifted populations: drho = sum g, j = sum c g.
 template <int Q>
@@ -135,8 +145,13 @@ __device__ __forceinline__ void moments(const float (&g)[Q], float &drho, float 
 // Moments: rho = 1 + drho, drho = sum g, j = sum c g, u = (j + F/2) / rho.
 // Each fmaf is one rounding; compiled without FMA contraction the sequence
 // of roundings is fixed, so every kernel gives the same bits for a cell.
+struct Vel {
+    float x, y, z;
+};
+
+// Returns the velocity u of the cell (unscaled), used by boundary links.
 template <int Q, bool SCALED>
-__device__ __forceinline__ void collide(float (&g)[Q], const CollideParams &p) {
+__device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
     constexpr int NP = (Q - 1) / 2;
     float s[NP], d[NP];
 #pragma unroll
@@ -196,6 +211,7 @@ __device__ __forceinline__ void collide(float (&g)[Q], const CollideParams &p) {
         g[i] = g[i] + (dp + dm);
         g[i + 1] = g[i + 1] + (dp - dm);
     }
+    return Vel{ux, uy, uz};
 }
 
 // Shifted equilibrium of (rho, u) (Eq. 6 minus w_i).

@@ -57,6 +57,8 @@ struct Domain {
     DevBuf P;                          // (Q-1) x S odd-step slots R(i,k) (row-flipped pull entries)
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
+    DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity
+    int64_t n_bcells = 0;
     DevBuf mask;                       // per-voxel link mask (dense)
     DevBuf red_partial;                // per-chunk FP64 partial sums
     DevBuf red_out;                    // 5 doubles
@@ -92,8 +94,10 @@ constexpr int RED_CHUNK = RED_THREADS * RED_CELLS_PER_THREAD;
 cudaError_t launch_unflip(const Domain &d, int32_t *out, cudaStream_t st);
 int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
                        int64_t n_inlet_u);
-// stream_collide.cu
+// aa_q19.cu / aa_q27.cu (dispatch in api.cu)
 cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st);
+// boundary fix-up before (post = 0) / after (post = 1) an even step
+cudaError_t launch_bc_fixup(const Domain &d, int post, cudaStream_t st);
 // macro.cu
 cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order, cudaStream_t st);
 cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st);

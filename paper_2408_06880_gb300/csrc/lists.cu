@@ -137,6 +137,18 @@ struct InletList {                 // ascending voxel ids of inlet voxels
     }
 };
 
+struct BoundaryCells {             // first link of each cell that has links
+    const int32_t *link_cell;
+    int32_t *bcell, *bfirst;
+    __device__ int32_t value(int64_t b) const { return b == 0 || link_cell[b - 1] != link_cell[b]; }
+    __device__ void emit(int64_t b, int32_t val, int32_t ex) const {
+        if (val) {
+            bcell[ex] = link_cell[b];
+            bfirst[ex] = (int32_t)b;
+        }
+    }
+};
+
 struct CountScan {                 // exclusive offsets of per-cell link counts
     const uint8_t *count;
     int32_t *offset;
@@ -244,6 +256,9 @@ __global__ void build_index(Box b, const uint8_t *flags, const int32_t *cell_id,
             link_dir[l] = i;
             link_type[l] = t;
             LinkMap m;
+            m.cx = (float)cx(i);
+            m.cy = (float)cy(i);
+            m.cz = (float)cz(i);
             if (t == FLAG_INLET) {
                 float ux = 0.f, uy = 0.f, uz = 0.f;
                 if (inlet_u) {
@@ -256,9 +271,11 @@ __global__ void build_index(Box b, const uint8_t *flags, const int32_t *cell_id,
                 }
                 m.s = 1.0f;
                 m.a = 6.0f * wgt<Q>(i) * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+                m.q2 = 0.0f;
             } else {
                 m.s = -1.0f;
                 m.a = 2.0f * wgt<Q>(i) * (rho_out - 1.0f);
+                m.q2 = 2.0f * wgt<Q>(i) * rho_out;
             }
             maps[l] = m;
         }
@@ -364,6 +381,20 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
     else launch(std::integral_constant<int, 27>{});
     if (cx.check(cudaGetLastError(), "build_index launch") || cx.check(cudaStreamSynchronize(cx.stream), "build sync"))
         return -1;
+    if (n_links > 0) {   // cells with links, for the fix-up around the even step
+        if (cx.alloc(d.bcell, n_links * 4) || cx.alloc(d.bfirst, (n_links + 1) * 4)) return -1;
+        int64_t nb = 0;
+        if (scan_run(cx, BoundaryCells{(const int32_t *)d.link_cell.p, (int32_t *)d.bcell.p, (int32_t *)d.bfirst.p},
+                     n_links, &nb))
+            return -1;
+        d.n_bcells = nb;
+        const int32_t end = (int32_t)n_links;
+        if (cx.check(cudaMemcpyAsync((int32_t *)d.bfirst.p + nb, &end, 4, cudaMemcpyHostToDevice, cx.stream),
+                     "bfirst end") ||
+            cx.alloc(d.bc_ubuf, nb * 3 * sizeof(float)) ||
+            cx.check(cudaStreamSynchronize(cx.stream), "boundary cells"))
+            return -1;
+    }
     cx.release(cell_id);
     cx.release(link_offset);
     cx.release(inlet_voxel);

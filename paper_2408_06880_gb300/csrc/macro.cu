@@ -33,13 +33,8 @@ struct SparseView {
                 g[i] = St::ld(pdf[i * S + k], inv_scale);
             } else {
                 const int32_t e = P[(i - 1) * S + k];
-                const int32_t r = e >= 0 ? e : i * S + k;
-                float v = St::ld(pdf[r], inv_scale);
-                if (e < 0) {
-                    const LinkMap m = maps[-(e + 1)];
-                    v = m.s * v + m.a;
-                }
-                g[i] = v;
+                const int32_t r = e >= 0 ? e : i * S + k;   // link slots already hold mapped values
+                g[i] = St::ld(pdf[r], inv_scale);
             }
         }
     }

@@ -441,27 +441,48 @@ slbm_status sync_table(slbm_pool *p) {
     return SLBM_OK;
 }
 
-cudaError_t launch_seq(slbm_pool *p, int32_t k) {
-    for (int32_t t = 0; t < k; ++t) {
-        const int mode = p->p0 < 0 ? 0 : 1 + 2 * ((p->p0 + t) & 1) + (p->uni ? 1 : 0);
-        if (p->ctas_per_sm == 0) {
-            TileKernel tk = p->q == 19 ? tile_kernel_for<19>(p->storage, mode, p->any_links)
-                                       : tile_kernel_for<27>(p->storage, mode, p->any_links);
-            const int v = (mode == 1 || mode == 2) ? 0 : 1;      // uniform even step: 256-cell tiles
-            if (p->n_tiles[v] == 0) continue;
-            tk<<<(unsigned)p->n_tiles[v], POOL_THREADS, 0, p->stream>>>(
-                (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up);
-            const cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            continue;
-        }
-        PoolKernel kern = kernel_of(p, mode);
-        kern<<<p->grid[mode], p->threads, 0, p->stream>>>((const PoolHeader *)p->d_hdr, (const PoolEntry *)p->d_tab, t,
-                                                    p->d_abort, (int32_t *)p->d_status, p->up);
-        const cudaError_t e = cudaGetLastError();
+cudaError_t launch_one(slbm_pool *p, int32_t t);
+
+// Boundary fix-ups (before: post = 0, after: post = 1) of the members that
+// take an even step in launch t and have inlet/outlet links.
+cudaError_t member_fixups(slbm_pool *p, int32_t t, int post) {
+    if (!p->any_links) return cudaSuccess;
+    for (size_t r = 0; r < p->order.size(); ++r) {
+        const PoolEntry &E = p->host_tab[r];
+        if (E.n_links == 0 || ((E.parity0 + t) & 1) != 0) continue;
+        const cudaError_t e = launch_bc_fixup(p->members[p->order[r]]->d, post, p->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_seq(slbm_pool *p, int32_t k) {
+    for (int32_t t = 0; t < k; ++t) {
+        cudaError_t fe = member_fixups(p, t, 0);
+        if (fe != cudaSuccess) return fe;
+        const cudaError_t le = launch_one(p, t);
+        if (le != cudaSuccess) return le;
+        fe = member_fixups(p, t, 1);
+        if (fe != cudaSuccess) return fe;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_one(slbm_pool *p, int32_t t) {
+    const int mode = p->p0 < 0 ? 0 : 1 + 2 * ((p->p0 + t) & 1) + (p->uni ? 1 : 0);
+    if (p->ctas_per_sm == 0) {
+        TileKernel tk = p->q == 19 ? tile_kernel_for<19>(p->storage, mode, p->any_links)
+                                   : tile_kernel_for<27>(p->storage, mode, p->any_links);
+        const int v = (mode == 1 || mode == 2) ? 0 : 1;      // uniform even step: 256-cell tiles
+        if (p->n_tiles[v] == 0) return cudaSuccess;
+        tk<<<(unsigned)p->n_tiles[v], POOL_THREADS, 0, p->stream>>>(
+            (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up);
+        return cudaGetLastError();
+    }
+    PoolKernel kern = kernel_of(p, mode);
+    kern<<<p->grid[mode], p->threads, 0, p->stream>>>((const PoolHeader *)p->d_hdr, (const PoolEntry *)p->d_tab, t,
+                                                p->d_abort, (int32_t *)p->d_status, p->up);
+    return cudaGetLastError();
 }
 
 }  // namespace
