@@ -175,8 +175,8 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
  * variant 2: odd step only, as variant 0 with 1 cell per thread, plus an
  *            asynchronous bulk L2 prefetch of the index-list rows of the block
  *            that will run one residency wave later.
- * Defaults: variant 0, 64 x 2 (even; FP16: variant 1, 128 x 2) and 64 x 1
- * (odd).  Results are bit-for-bit the same for every shape. */
+ * Defaults: even variant 0, 64 x 2 (FP16: variant 1, 128 x 2); odd variant 2,
+ * 128 x 1.  Results are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch

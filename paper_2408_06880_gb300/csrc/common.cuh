@@ -133,6 +133,10 @@ __device__ __forceinline__ void moments(const float (&g)[Q], float &drho, float 
     }
 }
 
+struct Vel {
+    float x, y, z;
+};
+
 // Collision in place (Eq. 3) on shifted populations held in stored units
 // (g * sigma; sigma = 1 for FP32).  TRT on each pair (i, inverse(i)) with
 // s = g_i + g_inv and d = g_i - g_inv: the even part s/2 relaxes towards
@@ -143,13 +147,13 @@ __device__ __forceinline__ void moments(const float (&g)[Q], float &drho, float 
 // split into its even part w (9 cu cF - 3 u.F) and odd part 3 w cF, each
 // weighted by (1 - omega/2) of its rate.  SRT (Eq. 5) is omega- = omega+.
 // Moments: rho = 1 + drho, drho = sum g, j = sum c g, u = (j + F/2) / rho.
-// Each fmaf is one rounding; compiled without FMA contraction the sequence
-// of roundings is fixed, so every kernel gives the same bits for a cell.
-struct Vel {
-    float x, y, z;
-};
-
-// Returns the velocity u of the cell (unscaled), used by boundary links.
+//
+// Written per pair as  g_i' = A + B,  g_inv' = A - B  with
+//   A = (1 - omega+)/2 s + omega+ g^eq+ + (1 - omega+/2) S+
+//   B = (1 - omega-)/2 d + omega- g^eq- + (1 - omega-/2) S-
+// and the terms that depend only on the weight class folded per cell.  Each
+// fmaf is one rounding; compiled without FMA contraction the sequence of
+// roundings is fixed, so every kernel gives the same bits for a cell.
 template <int Q, bool SCALED>
 __device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
     constexpr int NP = (Q - 1) / 2;
@@ -188,10 +192,13 @@ __device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
     const float sr = SCALED ? p.scale * rho : rho;              // sigma rho
     const float sE = SCALED ? p.scale * E : E;                  // sigma (drho - 1.5 rho u.u)
     const float skF = SCALED ? p.scale * (p.kp * 3.0f * uF) : p.kp * 3.0f * uF;  // sigma kp 3 u.F
+    const float wp = p.omega_p, wm = p.omega_m;
+    const float hp = 0.5f - 0.5f * wp, hm = 0.5f - 0.5f * wm;   // (1 - omega)/2
+    const float pE = wp * sE, pR = wp * sr, mR = wm * sr;
     // rest population: even only
     {
         constexpr float w = wgt<Q>(0);
-        g[0] = fmaf(p.omega_p, fmaf(w, sE, -g[0]), g[0]) - w * skF;
+        g[0] = fmaf(w, pE, fmaf(-wp, g[0], g[0])) - w * skF;
     }
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
@@ -204,12 +211,14 @@ __device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
         if (cy(i) < 0) cu -= uy;
         if (cz(i) > 0) cu += uz;
         if (cz(i) < 0) cu -= uz;
-        const float eqp = fmaf((4.5f * w) * sr, cu * cu, w * sE);   // sigma g^eq+
-        const float eqm = ((3.0f * w) * sr) * cu;                   // sigma g^eq-
-        const float dp = fmaf(p.omega_p, fmaf(-0.5f, s[m], eqp), fmaf(p.alpha[m], cu, -(w * skF)));
-        const float dm = fmaf(p.omega_m, fmaf(-0.5f, d[m], eqm), p.kappa[m]);
-        g[i] = g[i] + (dp + dm);
-        g[i + 1] = g[i + 1] + (dp - dm);
+        // class constants (folded by the compiler per weight class)
+        const float Ap = fmaf(w, pE, -(w * skF));               // omega+ w sE - w skF
+        const float Bp = (4.5f * w) * pR;                        // omega+ 4.5 w sigma rho
+        const float Cm = (3.0f * w) * mR;                        // omega- 3 w sigma rho
+        const float A = fmaf(hp, s[m], fmaf(Bp, cu * cu, fmaf(p.alpha[m], cu, Ap)));
+        const float B = fmaf(hm, d[m], fmaf(Cm, cu, p.kappa[m]));
+        g[i] = A + B;
+        g[i + 1] = A - B;
     }
     return Vel{ux, uy, uz};
 }

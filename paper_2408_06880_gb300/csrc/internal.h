@@ -69,7 +69,7 @@ struct Domain {
     slbm_allocator hook{};
     bool has_hook = false;
     int64_t device_bytes = 0;
-    LaunchShape shape[2] = {{64, 2, 0}, {64, 1, 0}};
+    LaunchShape shape[2] = {{64, 2, 0}, {128, 1, 2}};
     bool checked = false;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, parity) -> exec
 
