@@ -166,15 +166,19 @@ slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step);
 slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
 
 /* Launch shape used for a parity (0 even, 1 odd), chosen by the autotuner.
- * variant 0: one thread per `cells` consecutive cells (even 1/2/4, odd 1/2),
+ * variant 0: `cells` cells per thread (even 1/2/4 consecutive cells; odd 1/2
+ *            cells strided by the block size),
  *            `threads` per block (32..256, multiple of 32);
  * variant 1: persistent CTAs (SMs x resident CTAs) that walk tiles of
  *            `threads` cells (64 or 128) and keep `cells` tiles (2 or 4) of
  *            index-list rows (odd) or PDF rows (even) in flight in shared
  *            memory through asynchronous bulk copies; sparse FP32/FP16 only;
- * variant 2: odd step only, as variant 0 with 1 cell per thread, plus an
+ * variant 2: odd step only, as variant 0 (1 or 2 cells per thread), plus an
  *            asynchronous bulk L2 prefetch of the index-list rows of the block
- *            that will run one residency wave later.
+ *            that will run one residency wave later;
+ * variant 3: as variant 2, but each thread re-reads its slots from the list
+ *            before the scatter instead of keeping them in registers (domains
+ *            without inlet/outlet links; others run variant 2).
  * Defaults: even variant 0, 64 x 2 (FP16: variant 1, 128 x 2); odd variant 2,
  * 128 x 1.  Results are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);

@@ -43,6 +43,58 @@ __device__ __forceinline__ void st_vec(T *p, const Vec<T, N> &x) {
     *reinterpret_cast<Vec<T, N> *>(p) = x;
 }
 
+// A row segment of CPT consecutive cells: stored values <-> floats in stored
+// units.  FP16 pairs convert with the packed half2 forms (same rounding as
+// element-wise conversion, half the instructions on the store side).
+template <int ST, int CPT>
+struct RowIO {
+    using St = Store<ST>;
+    using T = typename St::T;
+    static __device__ __forceinline__ void load(const T *p, float (&f)[CPT]) {
+        const Vec<T, CPT> x = ld_vec<T, CPT>(p);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) f[c] = St::raw(x.v[c]);
+    }
+    static __device__ __forceinline__ Vec<T, CPT> pack(const float (&f)[CPT]) {
+        Vec<T, CPT> y;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(f[c]);
+        return y;
+    }
+};
+
+template <int CPT>
+struct RowIO<ST_F16, CPT> {
+    static_assert(CPT == 1 || CPT % 2 == 0, "FP16 rows: 1 or an even number of cells");
+    static __device__ __forceinline__ void load(const __half *p, float (&f)[CPT]) {
+        if constexpr (CPT == 1) {
+            f[0] = __half2float(*p);
+        } else {
+            const Vec<__half2, CPT / 2> x = ld_vec<__half2, CPT / 2>(reinterpret_cast<const __half2 *>(p));
+#pragma unroll
+            for (int c = 0; c < CPT / 2; ++c) {
+                const float2 v = __half22float2(x.v[c]);
+                f[2 * c] = v.x;
+                f[2 * c + 1] = v.y;
+            }
+        }
+    }
+    static __device__ __forceinline__ Vec<__half, CPT> pack(const float (&f)[CPT]) {
+        Vec<__half, CPT> y;
+        if constexpr (CPT == 1) {
+            y.v[0] = __float2half_rn(f[0]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPT / 2; ++c) {
+                const __half2 h = __floats2half2_rn(f[2 * c], f[2 * c + 1]);
+                y.v[2 * c] = __low2half(h);
+                y.v[2 * c + 1] = __high2half(h);
+            }
+        }
+        return y;
+    }
+};
+
 // Index entries are read once per odd step: stream them past L2 (evict-first).
 template <int N>
 __device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
@@ -77,18 +129,20 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
     float g[CPT][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + i * S + k0);
+        float f[CPT];
+        RowIO<ST, CPT>::load(pdf + i * S + k0, f);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) g[c][i] = St::raw(x.v[c]);
+        for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
     }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
     const bool full = k0 + CPT <= nf;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        Vec<T, CPT> y;
+        float f[CPT];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(g[c][i]);
+        for (int c = 0; c < CPT; ++c) f[c] = g[c][i];
+        const Vec<T, CPT> y = RowIO<ST, CPT>::pack(f);
         T *dst = pdf + inv(i) * S + k0;
         if (full) {
             st_vec<T, CPT>(dst, y);
@@ -107,42 +161,56 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // pf_dist > 0 (CPT = 1 only): thread 0 first asks the bulk-copy engine to
 // prefetch into L2 the index-list rows of the CTA pf_dist blocks ahead -- about
 // one residency wave later -- so that CTA's first round trip hits L2.
-template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK>
+// RELOAD (CPT = 1, no links): the slots are re-read from the list (an L1
+// hit) before the scatter instead of being held in registers through the
+// collision, which frees registers for more resident threads.
+// CPT cells per thread, strided by the block size (cell c of thread t in block
+// b is b*blockDim*CPT + c*blockDim + t), so that every load and store
+// instruction of a warp covers consecutive cells.
+// pf_dist > 0: thread 0 first asks the bulk-copy engine to prefetch into L2
+// the index-list rows of the block pf_dist blocks ahead -- about one residency
+// wave later -- so that block's first round trip hits L2.
+// RELOAD (CPT = 1, no links): the slots are re-read from the list (an L1
+// hit) before the scatter instead of being held in registers through the
+// collision, which frees registers for more resident threads.
+template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false>
 __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                      const int32_t *__restrict__ P, int32_t S, int32_t nf,
                                                      const LinkMap *__restrict__ maps, int32_t n_links,
                                                      CollideParams p, int32_t *err, int32_t pf_dist) {
     using St = Store<ST>;
     using T = typename St::T;
-    if (CPT == 1 && pf_dist > 0 && threadIdx.x == 0) {
-        const int64_t c0 = ((int64_t)blockIdx.x + pf_dist) * blockDim.x;
+    const int32_t span = blockDim.x * CPT;
+    if (pf_dist > 0 && threadIdx.x == 0) {
+        const int64_t c0 = ((int64_t)blockIdx.x + pf_dist) * span;
         if (c0 < nf) {
             const int64_t left = (int64_t)S - c0;
-            const uint32_t bytes = (uint32_t)(left < (int64_t)blockDim.x ? left : (int64_t)blockDim.x) * 4u;
+            const uint32_t bytes = (uint32_t)(left < (int64_t)span ? left : (int64_t)span) * 4u;
 #pragma unroll
             for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(P + r * S + c0, bytes);
         }
     }
-    const int32_t k0 = (blockIdx.x * blockDim.x + threadIdx.x) * CPT;
-    if (k0 >= nf) return;
+    const int32_t kb = blockIdx.x * span + threadIdx.x;
+    if (kb >= nf) return;
     int32_t e[CPT][Q];
+    bool valid[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) valid[c] = kb + c * (int32_t)blockDim.x < nf;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const Vec<int32_t, CPT> x = ld_index<CPT>(P + (i - 1) * S + k0);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) e[c][i] = x.v[c];
+        for (int c = 0; c < CPT; ++c) {
+            const int32_t k = kb + c * blockDim.x;
+            if (RELOAD) e[c][i] = P[(i - 1) * S + k];
+            else e[c][i] = valid[c] ? __ldcs(P + (i - 1) * S + k) : 0;
+        }
     }
     float g[CPT][Q];
     int32_t R[CPT][Q];
-    {
-        const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + k0);
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) g[c][0] = St::raw(x.v[c]);
-    }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        const int32_t k = k0 + c;
-        const bool valid = (CPT == 1) || k < nf;
+        const int32_t k = kb + c * blockDim.x;
+        g[c][0] = valid[c] ? St::raw(pdf[k]) : 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             int32_t ee = e[c][i];
@@ -156,28 +224,22 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
                 }
             }
             R[c][i] = r;
-            if (valid) g[c][i] = St::raw(pdf[r]);
-            else g[c][i] = 0.f;
+            g[c][i] = valid[c] ? St::raw(pdf[r]) : 0.f;
         }
     }
     Vel u[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) u[c] = collide<Q, St::scaled>(g[c], p);
-    {
-        Vec<T, CPT> y;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) y.v[c] = St::pack(g[c][0]);
-        if (k0 + CPT <= nf) {
-            st_vec<T, CPT>(pdf + k0, y);
-        } else {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c)
-                if (k0 + c < nf) pdf[k0 + c] = y.v[c];
-        }
-    }
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        if (CPT > 1 && k0 + c >= nf) continue;
+        const int32_t k = kb + c * blockDim.x;
+        if (!valid[c]) continue;
+        pdf[k] = St::pack(g[c][0]);
+        if (RELOAD) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) pdf[__ldcs(P + (i - 1) * S + k)] = St::pack(g[c][inv(i)]);
+            continue;
+        }
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             float v = g[c][inv(i)];
@@ -186,6 +248,7 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
         }
     }
 }
+
 
 }  // namespace slbm
 
@@ -342,9 +405,11 @@ __global__ void __launch_bounds__(TILE) aa_odd_staged_kernel(typename Store<ST>:
     __syncthreads();
 }
 
-template <int Q, int ST, int TILE, int NSTAGE>
-__global__ void __launch_bounds__(TILE) aa_even_staged_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
-                                                              int32_t nf, CollideParams p, int32_t *err) {
+// TILE cells per tile, CPT consecutive cells per thread (TILE / CPT threads).
+template <int Q, int ST, int TILE, int NSTAGE, int CPT = 1>
+__global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Store<ST>::T *__restrict__ pdf,
+                                                                    int32_t S, int32_t nf, CollideParams p,
+                                                                    int32_t *err) {
     using St = Store<ST>;
     using T = typename St::T;
     __shared__ __align__(128) T tile[NSTAGE][Q][TILE];
@@ -376,10 +441,15 @@ __global__ void __launch_bounds__(TILE) aa_even_staged_kernel(typename Store<ST>
         const int s = it % NSTAGE;
         const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
         const bool ok = mbar_wait_bounded(&bar[s], ph);
-        float g[Q];
+        float g[CPT][Q];
         if (ok) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = St::raw(tile[s][i][tid]);
+            for (int i = 0; i < Q; ++i) {
+                float f[CPT];
+                RowIO<ST, CPT>::load(&tile[s][i][CPT * tid], f);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
+            }
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) latch(err, ERR_STAGE_TIMEOUT);
@@ -391,11 +461,26 @@ __global__ void __launch_bounds__(TILE) aa_even_staged_kernel(typename Store<ST>
             const int32_t tn = t + NSTAGE * gridDim.x;
             if (tn < n_tiles) issue(tn, s);
         }
-        const int32_t k = t * TILE + tid;
-        if (k < nf) {
-            collide<Q, St::scaled>(g, p);
+        const int32_t k0 = t * TILE + CPT * tid;
+        if (k0 < nf) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) pdf[inv(i) * S + k] = St::pack(g[i]);
+            for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+            const bool full = k0 + CPT <= nf;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float f[CPT];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) f[c] = g[c][i];
+                const Vec<T, CPT> y = RowIO<ST, CPT>::pack(f);
+                T *dst = pdf + inv(i) * S + k0;
+                if (full) {
+                    st_vec<T, CPT>(dst, y);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c)
+                        if (k0 + c < nf) dst[c] = y.v[c];
+                }
+            }
         }
     }
     if (tid == 0 && ss.pending) drain_stages<NSTAGE>(bar, ss);

@@ -40,8 +40,13 @@ static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const int64_t tiles = S / TILE;
     if (parity == 0) {
-        auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE>;
-        k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err);
+        if constexpr (ST == ST_F16) {    // FP16: 2 cells per thread, paired conversions
+            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2>;
+            k<<<persistent_grid(k, TILE / 2, tiles), TILE / 2, 0, st>>>(pdf, S, nf, p, err);
+        } else {
+            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 1>;
+            k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err);
+        }
     } else {
         const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
         const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
@@ -97,7 +102,7 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
     const LaunchShape sh = d.shape[parity];
-    if (sh.variant == 2 && parity == 0) return cudaErrorInvalidValue;
+    if (sh.variant >= 2 && parity == 0) return cudaErrorInvalidValue;
     if (sh.variant == 1 && !d.checked && ST != ST_BF16) {
         switch (sh.threads * 10 + sh.cells) {
             case 642: return launch_staged<Q, ST, 64, 2>(d, parity, st);
@@ -128,17 +133,25 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
         else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0);
         return cudaGetLastError();
     }
+    // variant 3: slots re-read before the scatter (no links), with the L2 prefetch
+    if (sh.variant == 3 && !bc) {
+        auto kr = aa_odd_kernel<Q, ST, 1, false, false, true>;
+        const int32_t pfr = (int32_t)persistent_grid(kr, sh.threads, INT32_MAX);
+        kr<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfr);
+        return cudaGetLastError();
+    }
     // variant 2: L2 prefetch of the index rows one residency wave ahead
     int32_t pf = 0;
-    if (sh.variant == 2 && sh.cells == 1) {
-        auto kp = bc ? aa_odd_kernel<Q, ST, 1, true, false> : aa_odd_kernel<Q, ST, 1, false, false>;
+    if (sh.variant == 2 || sh.variant == 3) {
+        auto kp = sh.cells == 1 ? (bc ? aa_odd_kernel<Q, ST, 1, true, false> : aa_odd_kernel<Q, ST, 1, false, false>)
+                                : (bc ? aa_odd_kernel<Q, ST, 2, true, false> : aa_odd_kernel<Q, ST, 2, false, false>);
         pf = (int32_t)persistent_grid(kp, sh.threads, INT32_MAX);
     }
     switch (sh.cells * 2 + (bc ? 1 : 0)) {
         case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
         case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
-        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0); break;
-        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0); break;
+        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
+        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

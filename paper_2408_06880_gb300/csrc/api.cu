@@ -479,11 +479,12 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variant covers sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
-    } else if (variant == 2) {
-        if (parity != 1 || cells != 1 || threads < 32 || threads > 256 || threads % 32)
-            return err(SLBM_EINVAL, "variant 2 is for the odd step: threads 32..256 (multiple of 32), cells 1");
+    } else if (variant == 2 || variant == 3) {
+        if (parity != 1 || threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant == 2 && cells == 2)))
+            return err(SLBM_EINVAL, "variants 2 and 3 are for the odd step: threads 32..256 (multiple of 32), "
+                                    "cells 1 (variant 2 also 2)");
     } else {
-        return err(SLBM_EINVAL, "variant must be 0, 1 or 2");
+        return err(SLBM_EINVAL, "variant must be 0, 1, 2 or 3");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);
