@@ -74,6 +74,7 @@ def parse():
                     help="serve mode: all at t=0, or Poisson arrivals at --load x the measured capacity")
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--sequential", action="store_true", help="serve mode: also time one-at-a-time solves")
+    ap.add_argument("--pool-graph", type=int, default=1, help="serve mode: replay pool steps as CUDA graphs")
     a = ap.parse_args()
     if a.lbm_steps % 2:
         raise SystemExit("--lbm-steps must be even (whole AA pairs)")
@@ -431,8 +432,9 @@ def run_serve(a):
            "config": {"workload": f"{a.requests} permeability requests: periodic Boolean packings, edge "
                                   f"{{64,96,128,192}}, porosity U(0.3,0.8), D3Q19 TRT F=1e-6, converge to "
                                   f"1e-6 relative change of mean u_x per 100 steps or {a.max_steps} steps",
-                      "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals}}
-    ex = GpuExecutor(Q, storage, capacity=a.capacity)
+                      "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals,
+                      "pool_graph": bool(a.pool_graph)}}
+    ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph))
     srv = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()

@@ -264,9 +264,15 @@ slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem);
  * with `threads` cells per tile (32..128, multiple of 32) and at most
  * ctas_per_sm CTAs per SM. */
 slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm);
-/* raise != 0: set the host-mapped abort word; running and queued pool launches
- * stop at their next tile and the members' states are left part-way through
- * a step (restore them from a checkpoint).  raise == 0: wait for the pool's
+/* Members with at least split_cells fluid cells (default 524288) are stepped
+ * by their own single-domain kernels inside the pool's launch sequence (and
+ * graph); smaller members share the batched launch.  0 = batch every member.
+ * Applies to the tile-grid variant. */
+slbm_status slbm_pool_set_split(slbm_pool_t *p, int64_t split_cells);
+/* raise != 0: set the host-mapped abort word; running and queued batched pool
+ * launches stop at their next tile (members stepped by their own kernels
+ * finish theirs) and the members' states are left part-way through a step
+ * (restore them from a checkpoint).  raise == 0: wait for the pool's
  * stream, then clear the word and the latched status. */
 slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise);
 void slbm_pool_free(slbm_pool_t *p);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "slbm_pool_reduce": (_st, [_vp, _vp, _i32]),
     "slbm_pool_set_launch": (_st, [_vp, _i32, _i32]),
     "slbm_pool_abort": (_st, [_vp, _i32]),
+    "slbm_pool_set_split": (_st, [_vp, _i64]),
     "slbm_pool_free": (None, [_vp]),
 }
 

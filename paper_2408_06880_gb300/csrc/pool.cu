@@ -181,16 +181,29 @@ __global__ void fill_tiles(const PoolEntry *__restrict__ tab, int32_t n_dom, int
 // PARITY: 0 / 1 uniform, -1 mixed (per member, from its table row).
 // UNI: uniform collision constants in `up`.  BC: handle inlet/outlet links.
 // CPT: cells per thread (2 only for the uniform even step).
+// pf_dist > 0 (odd step): thread 0 also asks the bulk-copy engine to
+// prefetch into L2 the slot-list rows of the tile pf_dist ahead (about one
+// residency wave later).
 template <int Q, int ST, int PARITY, bool UNI, bool BC, int CPT>
 __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry *__restrict__ tab,
                                                                  const TileDesc *__restrict__ tiles,
                                                                  int32_t seq_step,
                                                                  const volatile int32_t *abort_flag,
                                                                  int32_t *stop,
-                                                                 const __grid_constant__ CollideParams up) {
+                                                                 const __grid_constant__ CollideParams up,
+                                                                 int32_t n_tiles, int32_t pf_dist) {
     using St = Store<ST>;
     using T = typename St::T;
     const int32_t t = blockIdx.x;
+    if (PARITY == 1 && pf_dist > 0 && threadIdx.x == 0 && t + pf_dist < n_tiles) {
+        const TileDesc F = tiles[t + pf_dist];
+        const int32_t left = F.nf - F.first;
+        if (left > 0) {
+            const int32_t cells = ((left < POOL_THREADS ? left : POOL_THREADS) + 3) & ~3;   // whole 16 bytes
+#pragma unroll
+            for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(F.R + r * F.S + F.first, (uint32_t)cells * 4u);
+        }
+    }
     int32_t halt = *(volatile int32_t *)stop;
     if (!halt && (t & 255) == 0 && abort_flag && *abort_flag) {
         if (threadIdx.x == 0) atomicCAS(stop, 0, (int32_t)SLBM_EABORTED);
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
 }
 
 using TileKernel = void (*)(const PoolEntry *, const TileDesc *, int32_t, const volatile int32_t *, int32_t *,
-                            const CollideParams);
+                            const CollideParams, int32_t, int32_t);
 
 // mode: 0 mixed parity, 1 + 2*parity + uni
 template <int Q, int ST>
@@ -312,6 +325,9 @@ struct slbm_pool {
     bool dirty = true;
     int32_t threads = 64, ctas_per_sm = 0;   // ctas_per_sm > 0: persistent walker
     unsigned grid[5] = {0, 0, 0, 0, 0};      // persistent grid of each kernel variant
+    int32_t pf_dist = 0;                 // odd tile kernel: L2 prefetch distance (resident CTAs)
+    int64_t split = 1 << 19;             // members with >= split cells step with their own kernels
+    std::vector<int32_t> big;            // slots of those members
     int32_t p0 = -1;                     // common parity of all members, or -1
     bool uni = false;                    // all members share collision constants
     bool any_links = false;              // some member has inlet/outlet links
@@ -355,6 +371,12 @@ slbm_status size_grid(slbm_pool *p) {
         if (p->ctas_per_sm > 0) c = std::min(c, p->ctas_per_sm);
         p->grid[mode] = (unsigned)(std::max(sms, 1) * c);
     }
+    int c = 1;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &c, p->q == 19 ? tile_kernel_for<19>(p->storage, 4, false) : tile_kernel_for<27>(p->storage, 4, false),
+        POOL_THREADS, 0);
+    if (e != cudaSuccess) return pcuda(e, "occupancy");
+    p->pf_dist = std::max(sms, 1) * std::max(c, 1);
     return SLBM_OK;
 }
 
@@ -367,11 +389,16 @@ slbm_status sync_table(slbm_pool *p) {
     if (!p->dirty) return SLBM_OK;
     p->host_tab.clear();
     p->order.clear();
+    p->big.clear();
     int32_t tile = 0;
     for (int32_t s = 0; s < p->capacity; ++s) {
         slbm_t *h = p->members[s];
         if (!h) continue;
         const Domain &d = h->d;
+        if (p->ctas_per_sm == 0 && p->split > 0 && d.n_fluid >= p->split) {
+            p->big.push_back(s);
+            continue;
+        }
         PoolEntry E{};
         E.pdf = d.pdf.p;
         E.R = (const int32_t *)d.P.p;
@@ -456,14 +483,25 @@ cudaError_t member_fixups(slbm_pool *p, int32_t t, int post) {
     return cudaSuccess;
 }
 
+// Launches of one step: the batched kernel over the small members (with the
+// boundary fix-ups of those at an even step), then every large member's own
+// AA step (which brings its own fix-ups), at parity (step at sequence start
+// + t).
 cudaError_t launch_seq(slbm_pool *p, int32_t k) {
     for (int32_t t = 0; t < k; ++t) {
-        cudaError_t fe = member_fixups(p, t, 0);
-        if (fe != cudaSuccess) return fe;
-        const cudaError_t le = launch_one(p, t);
-        if (le != cudaSuccess) return le;
-        fe = member_fixups(p, t, 1);
-        if (fe != cudaSuccess) return fe;
+        if (!p->host_tab.empty()) {
+            cudaError_t fe = member_fixups(p, t, 0);
+            if (fe != cudaSuccess) return fe;
+            const cudaError_t le = launch_one(p, t);
+            if (le != cudaSuccess) return le;
+            fe = member_fixups(p, t, 1);
+            if (fe != cudaSuccess) return fe;
+        }
+        for (int32_t s : p->big) {
+            const Domain &d = p->members[s]->d;
+            const cudaError_t e = launch_aa_step(d, (int)((d.step + t) & 1), p->stream);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -475,8 +513,10 @@ cudaError_t launch_one(slbm_pool *p, int32_t t) {
                                    : tile_kernel_for<27>(p->storage, mode, p->any_links);
         const int v = (mode == 1 || mode == 2) ? 0 : 1;      // uniform even step: 256-cell tiles
         if (p->n_tiles[v] == 0) return cudaSuccess;
+        const int32_t pf = (mode == 3 || mode == 4) ? p->pf_dist : 0;
         tk<<<(unsigned)p->n_tiles[v], POOL_THREADS, 0, p->stream>>>(
-            (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up);
+            (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up,
+            p->n_tiles[v], pf);
         return cudaGetLastError();
     }
     PoolKernel kern = kernel_of(p, mode);
@@ -578,7 +618,7 @@ slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph) {
     }
     slbm_status st = sync_table(p);
     if (st != SLBM_OK) return st;
-    if (p->host_hdr.total_tiles > 0) {
+    if (p->host_hdr.total_tiles > 0 || !p->big.empty()) {
         cudaError_t e;
         if (use_graph) {
             const auto key = std::make_tuple((int)k, (int)p->p0, (p->uni ? 1 : 0) + (p->any_links ? 2 : 0));
@@ -651,6 +691,17 @@ slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_p
     p->dirty = true;
     drop_pool_graphs(p);
     return size_grid(p);
+}
+
+slbm_status slbm_pool_set_split(slbm_pool_t *p, int64_t split_cells) {
+    if (!p || split_cells < 0) return perr(SLBM_EINVAL, "need a pool and split_cells >= 0");
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pcuda(e, "pool split");
+    p->split = split_cells;
+    p->dirty = true;
+    drop_pool_graphs(p);
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
 }
 
 slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise) {

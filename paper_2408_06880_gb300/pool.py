@@ -68,5 +68,10 @@ class Pool:
     def set_launch(self, threads: int, ctas_per_sm: int = 0):
         A.check(A.lib().slbm_pool_set_launch(self.h, int(threads), int(ctas_per_sm)))
 
+    def set_split(self, split_cells: int):
+        """Members with >= split_cells fluid cells step with their own kernels
+        inside the pool's launch sequence; 0 batches every member."""
+        A.check(A.lib().slbm_pool_set_split(self.h, int(split_cells)))
+
     def abort(self, raise_flag: bool = True):
         A.check(A.lib().slbm_pool_abort(self.h, int(bool(raise_flag))))

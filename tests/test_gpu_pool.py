@@ -37,14 +37,18 @@ def _alone(g, kw, steps):
         return d.get_state()[0], d.reduce()
 
 
+@pytest.mark.parametrize("split", [0, 10000])
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
 @pytest.mark.parametrize("graph", [False, True])
-def test_pool_members_match_alone_bitwise(storage, graph):
+def test_pool_members_match_alone_bitwise(storage, graph, split):
+    # split 10000: the larger members step with their own kernels, the
+    # smaller ones share the batched launch
     cases = _cases(storage)
     steps = 9
     want = [_alone(g, kw, steps) for g, kw in cases]
     doms = [gpu_domain(g, **kw) for g, kw in cases]
     with P.Pool(19, storage, capacity=8) as pool:
+        pool.set_split(split)
         slots = [pool.add(d) for d in doms]
         pool.step(4, graph=graph)
         pool.step(5, graph=graph)
@@ -60,12 +64,14 @@ def test_pool_members_match_alone_bitwise(storage, graph):
         d.close()
 
 
-def test_mixed_parities_and_membership_changes_under_graph_replay():
+@pytest.mark.parametrize("split", [0, 10000])
+def test_mixed_parities_and_membership_changes_under_graph_replay(split):
     cases = _cases()
     (ga, ka), (gb, kb), (gc, kc), _ = cases
     a, b, c = gpu_domain(ga, **ka), gpu_domain(gb, **kb), gpu_domain(gc, **kc)
     a.step(3)                                  # a joins at odd parity
     with P.Pool(19, 0, capacity=4) as pool:
+        pool.set_split(split)
         sa, sb = pool.add(a), pool.add(b)
         pool.step(4, graph=True)               # a: 7, b: 4
         pool.remove(sa)
@@ -85,6 +91,7 @@ def test_abort_flag_stops_kernels_and_context_stays_usable():
     cases = _cases()
     doms = [gpu_domain(g, **kw) for g, kw in cases]
     with P.Pool(19, 0, capacity=8) as pool:
+        pool.set_split(0)                      # every member in the batched launch
         for d in doms:
             pool.add(d)
         pool.abort(True)
