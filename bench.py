@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--sequential", action="store_true", help="serve mode: also time one-at-a-time solves")
     ap.add_argument("--pool-graph", type=int, default=1, help="serve mode: replay pool steps as CUDA graphs")
+    ap.add_argument("--pool-streams", type=int, default=2, help="serve mode: streams of a pool step")
+    ap.add_argument("--group-mb", type=float, default=None,
+                    help="serve mode: L2 group size of the pool in MiB (0 = one group; default: the library's)")
     a = ap.parse_args()
     if a.lbm_steps % 2:
         raise SystemExit("--lbm-steps must be even (whole AA pairs)")
@@ -433,8 +436,11 @@ def run_serve(a):
                                   f"{{64,96,128,192}}, porosity U(0.3,0.8), D3Q19 TRT F=1e-6, converge to "
                                   f"1e-6 relative change of mean u_x per 100 steps or {a.max_steps} steps",
                       "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals,
-                      "pool_graph": bool(a.pool_graph)}}
-    ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph))
+                      "pool_graph": bool(a.pool_graph), "group_mb": a.group_mb,
+                      "pool_streams": a.pool_streams}}
+    ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph),
+                     group_bytes=None if a.group_mb is None else int(a.group_mb * 2 ** 20),
+                     streams=a.pool_streams)
     srv = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
@@ -454,12 +460,28 @@ def run_serve(a):
     out["results"] = [{"rid": r.rid, "k": r.permeability, "steps": r.steps, "converged": r.converged,
                        "latency_s": round(r.latency, 4), "error": r.error} for r in sorted(res, key=lambda r: r.rid)]
     if a.sequential:
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         alone = [solve_alone(r, storage=storage) for r in reqs]
         wall = time.perf_counter() - t0
-        out["one_at_a_time"] = {"solves_per_s": len(alone) / wall, "wall_s": wall}
+        lat = np.array([r.latency for r in alone])          # service time of each solve
+        seq = {"solves_per_s": len(alone) / wall, "wall_s": wall,
+               "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99))}
+        if a.arrivals == "poisson":
+            # a one-at-a-time FIFO server under the same arrivals, replayed
+            # from the measured service times
+            done, fifo = 0.0, []
+            for r, s in sorted(zip(reqs, lat), key=lambda x: (x[0].arrival, x[0].rid)):
+                done = max(done, r.arrival) + s
+                fifo.append(done - r.arrival)
+            seq["poisson_fifo"] = {"latency_p50_s": float(np.percentile(fifo, 50)),
+                                   "latency_p99_s": float(np.percentile(fifo, 99)),
+                                   "latency_mean_s": float(np.mean(fifo))}
+        out["one_at_a_time"] = seq
         k_alone = {r.rid: r.permeability for r in alone}
         out["served_equals_alone"] = all(r.permeability == k_alone[r.rid] for r in res if r.error is None)
+        steps_alone = {r.rid: r.steps for r in alone}
+        out["served_steps_equal_alone"] = all(r.steps == steps_alone[r.rid] for r in res if r.error is None)
     return out
 
 

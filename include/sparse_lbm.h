@@ -269,6 +269,23 @@ slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_p
  * graph); smaller members share the batched launch.  0 = batch every member.
  * Applies to the tile-grid variant. */
 slbm_status slbm_pool_set_split(slbm_pool_t *p, int64_t split_cells);
+/* Launch order of the tile-grid variant.  The batched members are cut, in
+ * slot order, into groups whose state + index + link-map bytes sum to at most
+ * `bytes` (default 48 MiB; a member larger than that is a group of its own);
+ * one slbm_pool_step(k) runs group after group, each for all k steps, then
+ * each large member for its k steps.  A group that fits in L2 streams its k
+ * steps from L2.  0 = one group of all batched members (every launch covers
+ * all of them).  Members are independent: the order changes no result. */
+slbm_status slbm_pool_set_group_bytes(slbm_pool_t *p, int64_t bytes);
+/* Streams of a graph step (use_graph != 0, tile-grid variant): n == 1
+ * (default) runs everything in order on the pool's stream.  n > 1 (at most
+ * 16) forks n - 1 extra streams, owned by the pool, from the pool's stream:
+ * the batched groups stay on the pool's stream, each large member goes to the
+ * stream with the fewest fluid cells queued in this step, and the pool's
+ * stream waits for all of them before the step returns.  Work on the pool's
+ * stream after the step (reduce, remove, free) sees every member finished.
+ * Members are independent: the spread changes no result. */
+slbm_status slbm_pool_set_streams(slbm_pool_t *p, int32_t n);
 /* raise != 0: set the host-mapped abort word; running and queued batched pool
  * launches stop at their next tile (members stepped by their own kernels
  * finish theirs) and the members' states are left part-way through a step

@@ -79,6 +79,8 @@ SIGNATURES = {
     "slbm_pool_set_launch": (_st, [_vp, _i32, _i32]),
     "slbm_pool_abort": (_st, [_vp, _i32]),
     "slbm_pool_set_split": (_st, [_vp, _i64]),
+    "slbm_pool_set_group_bytes": (_st, [_vp, _i64]),
+    "slbm_pool_set_streams": (_st, [_vp, _i32]),
     "slbm_pool_free": (None, [_vp]),
 }
 

@@ -116,6 +116,33 @@ static cudaError_t launch_one_step(const Domain &d, int parity, cudaStream_t st)
     return d.layout == SLBM_LAYOUT_SPARSE ? launch_aa_step(d, parity, st) : launch_dense_step(d, parity, st);
 }
 
+// The domain's cached graph of n steps from its current parity, captured on
+// first use (capture records launches only; it runs nothing).
+cudaError_t domain_graph(Domain &d, int32_t n, cudaGraphExec_t *out) {
+    const std::pair<int, int> key(n, (int)(d.step & 1));
+    auto it = d.graphs.find(key);
+    if (it == d.graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t le = cudaSuccess;
+        for (int32_t t = 0; t < n && le == cudaSuccess; ++t) le = launch_one_step(d, (int)((d.step + t) & 1), d.stream);
+        e = cudaStreamEndCapture(d.stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return le;
+        }
+        if (e != cudaSuccess) return e;
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        it = d.graphs.emplace(key, ex).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
+}
+
 static void drop_graphs(Domain &d) {
     for (auto &kv : d.graphs) cudaGraphExecDestroy(kv.second);
     d.graphs.clear();
@@ -283,27 +310,10 @@ slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n) {
     if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
     if (n == 0) return ok();
     Domain &d = h->d;
-    const std::pair<int, int> key(n, (int)(d.step & 1));
-    auto it = d.graphs.find(key);
-    if (it == d.graphs.end()) {
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_err(e, "begin capture");
-        cudaError_t le = cudaSuccess;
-        for (int32_t t = 0; t < n && le == cudaSuccess; ++t) le = launch_one_step(d, (int)((d.step + t) & 1), d.stream);
-        e = cudaStreamEndCapture(d.stream, &g);
-        if (le != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return cuda_err(le, "launch during capture");
-        }
-        if (e != cudaSuccess) return cuda_err(e, "end capture");
-        cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_err(e, "graph instantiate");
-        it = d.graphs.emplace(key, ex).first;
-    }
-    const cudaError_t e = cudaGraphLaunch(it->second, d.stream);
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = domain_graph(d, n, &ex);
+    if (e != cudaSuccess) return cuda_err(e, "graph capture");
+    e = cudaGraphLaunch(ex, d.stream);
     if (e != cudaSuccess) return cuda_err(e, "graph launch");
     d.step += n;
     return ok();

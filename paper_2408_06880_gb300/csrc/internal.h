@@ -98,6 +98,9 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
 cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st);
 // boundary fix-up before (post = 0) / after (post = 1) an even step
 cudaError_t launch_bc_fixup(const Domain &d, int post, cudaStream_t st);
+// The domain's cached CUDA graph of n steps from its current parity (captured
+// on first use); launch it on any stream.
+cudaError_t domain_graph(Domain &d, int32_t n, cudaGraphExec_t *out);
 // macro.cu
 cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order, cudaStream_t st);
 cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st);

@@ -323,11 +323,25 @@ struct slbm_pool {
     int32_t *h_abort = nullptr;          // host-mapped abort word
     int32_t *d_abort = nullptr;
     bool dirty = true;
+    bool table_ok = false;               // the device table and tiles match host_tab
+    // extra streams of a graph step: the batched groups and the large members
+    // are spread over the pool's stream and these, forked from and joined
+    // back into the pool's stream, so one member's tail overlaps another's
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_join;
+    cudaEvent_t fork = nullptr;
     int32_t threads = 64, ctas_per_sm = 0;   // ctas_per_sm > 0: persistent walker
     unsigned grid[5] = {0, 0, 0, 0, 0};      // persistent grid of each kernel variant
     int32_t pf_dist = 0;                 // odd tile kernel: L2 prefetch distance (resident CTAs)
     int64_t split = 1 << 19;             // members with >= split cells step with their own kernels
     std::vector<int32_t> big;            // slots of those members
+    // L2 groups: consecutive table rows whose summed state + index bytes stay
+    // within group_bytes; a group takes all k steps of a pool step before the
+    // next one starts, so a group that fits in L2 streams from L2 (0: one
+    // group of all rows)
+    int64_t group_bytes = 48ll << 20;
+    struct Group { int32_t r0, r1, t0[2], nt[2]; };
+    std::vector<Group> groups;
     int32_t p0 = -1;                     // common parity of all members, or -1
     bool uni = false;                    // all members share collision constants
     bool any_links = false;              // some member has inlet/outlet links
@@ -387,8 +401,10 @@ slbm_status sync_table(slbm_pool *p) {
         if (p->members[p->order[r]] && (int32_t)(p->members[p->order[r]]->d.step & 1) != p->host_tab[r].parity0)
             p->dirty = true;
     if (!p->dirty) return SLBM_OK;
-    p->host_tab.clear();
-    p->order.clear();
+    std::vector<PoolEntry> prev_tab;
+    std::vector<int32_t> prev_order;
+    prev_tab.swap(p->host_tab);
+    prev_order.swap(p->order);
     p->big.clear();
     int32_t tile = 0;
     for (int32_t s = 0; s < p->capacity; ++s) {
@@ -426,6 +442,44 @@ slbm_status sync_table(slbm_pool *p) {
         if (std::memcmp(&E.p, &p->host_tab[0].p, sizeof(CollideParams)) != 0) p->uni = false;
     }
     p->up = p->host_tab.empty() ? CollideParams{} : p->host_tab[0].p;
+    // first tile of every row in both tilings, and the L2 groups over them
+    const int32_t cells[2] = {2 * POOL_THREADS, POOL_THREADS};
+    const size_t nrow = p->host_tab.size();
+    std::vector<int32_t> begin[2] = {std::vector<int32_t>(nrow + 1), std::vector<int32_t>(nrow + 1)};
+    for (int v = 0; v < 2; ++v) {
+        int32_t n = 0;
+        for (size_t r = 0; r < nrow; ++r) {
+            begin[v][r] = n;
+            n += (p->host_tab[r].nf + cells[v] - 1) / cells[v];
+        }
+        begin[v][nrow] = n;
+    }
+    p->groups.clear();
+    {
+        const int64_t elt = p->storage == SLBM_FP32 ? 4 : 2;
+        int64_t acc = 0;
+        for (size_t r = 0; r < nrow; ++r) {
+            const PoolEntry &E = p->host_tab[r];
+            const int64_t bytes = (int64_t)E.S * (p->q * elt + (p->q - 1) * 4) + (int64_t)E.n_links * sizeof(LinkMap);
+            if (p->groups.empty() || (p->group_bytes > 0 && acc + bytes > p->group_bytes)) {
+                p->groups.push_back({(int32_t)r, (int32_t)r, {begin[0][r], begin[1][r]}, {0, 0}});
+                acc = 0;
+            }
+            acc += bytes;
+            slbm_pool::Group &G = p->groups.back();
+            G.r1 = (int32_t)r + 1;
+            for (int v = 0; v < 2; ++v) G.nt[v] = begin[v][r + 1] - G.t0[v];
+        }
+    }
+    // the batched table is unchanged (only large members came or went): the
+    // device table, the tiles and the batched graphs stay valid
+    static_assert(sizeof(PoolEntry) == 48 + sizeof(CollideParams), "PoolEntry has no padding");
+    if (p->table_ok && prev_order == p->order && prev_tab.size() == p->host_tab.size() &&
+        (prev_tab.empty() || std::memcmp(prev_tab.data(), p->host_tab.data(), prev_tab.size() * sizeof(PoolEntry)) == 0)) {
+        p->dirty = false;
+        return SLBM_OK;
+    }
+    p->table_ok = false;
     cudaError_t e = cudaSuccess;
     if (!p->host_tab.empty())
         e = cudaMemcpyAsync(p->d_tab, p->host_tab.data(), p->host_tab.size() * sizeof(PoolEntry),
@@ -434,14 +488,8 @@ slbm_status sync_table(slbm_pool *p) {
         e = cudaMemcpyAsync(p->d_hdr, &p->host_hdr, sizeof(PoolHeader), cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess && p->ctas_per_sm == 0 && tile > 0) {
         // tile descriptors for both tilings
-        const int32_t cells[2] = {2 * POOL_THREADS, POOL_THREADS};
-        std::vector<int32_t> begin(p->host_tab.size());
         for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-            int32_t n = 0;
-            for (size_t r = 0; r < p->host_tab.size(); ++r) {
-                begin[r] = n;
-                n += (p->host_tab[r].nf + cells[v] - 1) / cells[v];
-            }
+            const int32_t n = begin[v][nrow];
             p->n_tiles[v] = n;
             if (n > p->tiles_cap[v]) {
                 if (p->d_tiles[v]) cudaFree(p->d_tiles[v]);
@@ -450,7 +498,7 @@ slbm_status sync_table(slbm_pool *p) {
                 p->tiles_cap[v] = e == cudaSuccess ? n : 0;
             }
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(p->d_begin, begin.data(), begin.size() * sizeof(int32_t),
+                e = cudaMemcpyAsync(p->d_begin, begin[v].data(), nrow * sizeof(int32_t),
                                     cudaMemcpyHostToDevice, p->stream);
             if (e == cudaSuccess) {
                 fill_tiles<<<dim3(64, (unsigned)p->host_tab.size()), 256, 0, p->stream>>>(
@@ -465,16 +513,17 @@ slbm_status sync_table(slbm_pool *p) {
     if (e != cudaSuccess) return pcuda(e, "pool table upload");
     if (p->ctas_per_sm == 0) drop_pool_graphs(p);   // the tile grid follows the membership
     p->dirty = false;
+    p->table_ok = true;
     return SLBM_OK;
 }
 
-cudaError_t launch_one(slbm_pool *p, int32_t t);
+cudaError_t launch_one(slbm_pool *p, int32_t t, const slbm_pool::Group *g);
 
-// Boundary fix-ups (before: post = 0, after: post = 1) of the members that
-// take an even step in launch t and have inlet/outlet links.
-cudaError_t member_fixups(slbm_pool *p, int32_t t, int post) {
+// Boundary fix-ups (before: post = 0, after: post = 1) of the members of rows
+// [r0, r1) that take an even step in launch t and have inlet/outlet links.
+cudaError_t member_fixups(slbm_pool *p, int32_t t, int post, int32_t r0, int32_t r1) {
     if (!p->any_links) return cudaSuccess;
-    for (size_t r = 0; r < p->order.size(); ++r) {
+    for (int32_t r = r0; r < r1; ++r) {
         const PoolEntry &E = p->host_tab[r];
         if (E.n_links == 0 || ((E.parity0 + t) & 1) != 0) continue;
         const cudaError_t e = launch_bc_fixup(p->members[p->order[r]]->d, post, p->stream);
@@ -483,22 +532,42 @@ cudaError_t member_fixups(slbm_pool *p, int32_t t, int post) {
     return cudaSuccess;
 }
 
-// Launches of one step: the batched kernel over the small members (with the
-// boundary fix-ups of those at an even step), then every large member's own
-// AA step (which brings its own fix-ups), at parity (step at sequence start
-// + t).
-cudaError_t launch_seq(slbm_pool *p, int32_t k) {
-    for (int32_t t = 0; t < k; ++t) {
-        if (!p->host_tab.empty()) {
-            cudaError_t fe = member_fixups(p, t, 0);
-            if (fe != cudaSuccess) return fe;
-            const cudaError_t le = launch_one(p, t);
-            if (le != cudaSuccess) return le;
-            fe = member_fixups(p, t, 1);
-            if (fe != cudaSuccess) return fe;
+// k steps of every L2 group of batched members, group after group.
+cudaError_t launch_groups(slbm_pool *p, int32_t k) {
+    for (const slbm_pool::Group &g : p->groups) {
+        for (int32_t t = 0; t < k; ++t) {
+            cudaError_t e = member_fixups(p, t, 0, g.r0, g.r1);
+            if (e == cudaSuccess) e = launch_one(p, t, &g);
+            if (e == cudaSuccess) e = member_fixups(p, t, 1, g.r0, g.r1);
+            if (e != cudaSuccess) return e;
         }
-        for (int32_t s : p->big) {
-            const Domain &d = p->members[s]->d;
+    }
+    return cudaSuccess;
+}
+
+// k steps of every large member with its own kernels, member after member:
+// launched directly, or as each member's own cached graph (which outlives
+// changes of the pool's membership).
+cudaError_t launch_big(slbm_pool *p, int32_t k, bool graph) {
+    // with extra streams: each member on the stream with the fewest cells so
+    // far (the batched groups count on the pool's stream)
+    std::vector<int64_t> load(p->aux.size() + 1, 0);
+    if (graph)
+        for (const PoolEntry &E : p->host_tab) load[0] += E.nf;
+    for (int32_t s : p->big) {
+        Domain &d = p->members[s]->d;
+        if (graph) {
+            size_t j = 0;
+            for (size_t c = 1; c < load.size(); ++c)
+                if (load[c] < load[j]) j = c;
+            load[j] += d.n_fluid;
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t e = domain_graph(d, k, &ex);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ex, j == 0 ? p->stream : p->aux[j - 1]);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        for (int32_t t = 0; t < k; ++t) {
             const cudaError_t e = launch_aa_step(d, (int)((d.step + t) & 1), p->stream);
             if (e != cudaSuccess) return e;
         }
@@ -506,17 +575,61 @@ cudaError_t launch_seq(slbm_pool *p, int32_t k) {
     return cudaSuccess;
 }
 
-cudaError_t launch_one(slbm_pool *p, int32_t t) {
+// Every extra stream waits for the work queued so far on the pool's stream.
+cudaError_t fork_aux(slbm_pool *p) {
+    cudaError_t e = cudaEventRecord(p->fork, p->stream);
+    for (size_t j = 0; j < p->aux.size() && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(p->aux[j], p->fork, 0);
+    return e;
+}
+
+// The pool's stream waits for the work on every extra stream.
+cudaError_t join_aux(slbm_pool *p) {
+    for (size_t j = 0; j < p->aux.size(); ++j) {
+        cudaError_t e = cudaEventRecord(p->aux_join[j], p->aux[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->aux_join[j], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void free_aux(slbm_pool *p) {
+    for (cudaStream_t a : p->aux) cudaStreamDestroy(a);
+    for (cudaEvent_t ev : p->aux_join) cudaEventDestroy(ev);
+    p->aux.clear();
+    p->aux_join.clear();
+}
+
+// Launches of k steps, group-major: each L2 group of small members takes its
+// k batched steps (with the boundary fix-ups of its members at an even step),
+// then every large member its k own AA steps (which bring their own
+// fix-ups).  Launch t of a member is its step (step at sequence start + t);
+// members are independent, so the order across members changes no result.
+cudaError_t launch_seq(slbm_pool *p, int32_t k) {
+    if (p->ctas_per_sm > 0) {            // persistent walker: the whole table per launch
+        for (int32_t t = 0; t < k && !p->host_tab.empty(); ++t) {
+            cudaError_t e = member_fixups(p, t, 0, 0, (int32_t)p->host_tab.size());
+            if (e == cudaSuccess) e = launch_one(p, t, nullptr);
+            if (e == cudaSuccess) e = member_fixups(p, t, 1, 0, (int32_t)p->host_tab.size());
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const cudaError_t e = launch_groups(p, k);
+    return e != cudaSuccess ? e : launch_big(p, k, false);
+}
+
+cudaError_t launch_one(slbm_pool *p, int32_t t, const slbm_pool::Group *g) {
     const int mode = p->p0 < 0 ? 0 : 1 + 2 * ((p->p0 + t) & 1) + (p->uni ? 1 : 0);
     if (p->ctas_per_sm == 0) {
         TileKernel tk = p->q == 19 ? tile_kernel_for<19>(p->storage, mode, p->any_links)
                                    : tile_kernel_for<27>(p->storage, mode, p->any_links);
         const int v = (mode == 1 || mode == 2) ? 0 : 1;      // uniform even step: 256-cell tiles
-        if (p->n_tiles[v] == 0) return cudaSuccess;
+        const int32_t nt = g->nt[v];
+        if (nt == 0) return cudaSuccess;
         const int32_t pf = (mode == 3 || mode == 4) ? p->pf_dist : 0;
-        tk<<<(unsigned)p->n_tiles[v], POOL_THREADS, 0, p->stream>>>(
-            (const PoolEntry *)p->d_tab, p->d_tiles[v], t, p->d_abort, (int32_t *)p->d_status, p->up,
-            p->n_tiles[v], pf);
+        tk<<<(unsigned)nt, POOL_THREADS, 0, p->stream>>>(
+            (const PoolEntry *)p->d_tab, p->d_tiles[v] + g->t0[v], t, p->d_abort, (int32_t *)p->d_status, p->up,
+            nt, pf);
         return cudaGetLastError();
     }
     PoolKernel kern = kernel_of(p, mode);
@@ -619,8 +732,44 @@ slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph) {
     slbm_status st = sync_table(p);
     if (st != SLBM_OK) return st;
     if (p->host_hdr.total_tiles > 0 || !p->big.empty()) {
-        cudaError_t e;
-        if (use_graph) {
+        cudaError_t e = cudaSuccess;
+        if (use_graph && p->ctas_per_sm == 0) {
+            // the batched groups as the pool's graph, each large member as its own
+            if (!p->aux.empty()) {
+                e = fork_aux(p);
+                if (e != cudaSuccess) return pcuda(e, "pool fork");
+            }
+            if (!p->host_tab.empty()) {
+                const auto key = std::make_tuple((int)k, (int)p->p0, (p->uni ? 1 : 0) + (p->any_links ? 2 : 0));
+                auto it = p->graphs.find(key);
+                if (it != p->graphs.end() && p->uni &&
+                    std::memcmp(&it->second.second, &p->up, sizeof(CollideParams)) != 0) {
+                    cudaGraphExecDestroy(it->second.first);
+                    p->graphs.erase(it);
+                    it = p->graphs.end();
+                }
+                if (it == p->graphs.end()) {
+                    cudaGraph_t g = nullptr;
+                    e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+                    if (e != cudaSuccess) return pcuda(e, "begin capture");
+                    const cudaError_t le = launch_groups(p, k);
+                    e = cudaStreamEndCapture(p->stream, &g);
+                    if (le != cudaSuccess) {
+                        if (g) cudaGraphDestroy(g);
+                        return pcuda(le, "pool launch during capture");
+                    }
+                    if (e != cudaSuccess) return pcuda(e, "end capture");
+                    cudaGraphExec_t ex = nullptr;
+                    e = cudaGraphInstantiate(&ex, g, 0);
+                    cudaGraphDestroy(g);
+                    if (e != cudaSuccess) return pcuda(e, "graph instantiate");
+                    it = p->graphs.emplace(key, std::make_pair(ex, p->up)).first;
+                }
+                e = cudaGraphLaunch(it->second.first, p->stream);
+            }
+            if (e == cudaSuccess) e = launch_big(p, k, true);
+            if (e == cudaSuccess && !p->aux.empty()) e = join_aux(p);
+        } else if (use_graph) {
             const auto key = std::make_tuple((int)k, (int)p->p0, (p->uni ? 1 : 0) + (p->any_links ? 2 : 0));
             auto it = p->graphs.find(key);
             if (it != p->graphs.end() && p->uni &&
@@ -689,6 +838,7 @@ slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_p
     p->threads = threads;
     p->ctas_per_sm = ctas_per_sm;
     p->dirty = true;
+    p->table_ok = false;
     drop_pool_graphs(p);
     return size_grid(p);
 }
@@ -699,7 +849,44 @@ slbm_status slbm_pool_set_split(slbm_pool_t *p, int64_t split_cells) {
     if (e != cudaSuccess) return pcuda(e, "pool split");
     p->split = split_cells;
     p->dirty = true;
+    p->table_ok = false;
     drop_pool_graphs(p);
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+slbm_status slbm_pool_set_group_bytes(slbm_pool_t *p, int64_t bytes) {
+    if (!p || bytes < 0) return perr(SLBM_EINVAL, "need a pool and bytes >= 0");
+    const cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pcuda(e, "pool group bytes");
+    p->group_bytes = bytes;
+    p->dirty = true;
+    p->table_ok = false;
+    drop_pool_graphs(p);
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
+slbm_status slbm_pool_set_streams(slbm_pool_t *p, int32_t n) {
+    if (!p || n < 1 || n > 16) return perr(SLBM_EINVAL, "need a pool and 1 <= n <= 16");
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pcuda(e, "pool streams");
+    free_aux(p);
+    if (!p->fork) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    for (int32_t j = 1; j < n && e == cudaSuccess; ++j) {
+        cudaStream_t a = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+        if (e != cudaSuccess) break;
+        p->aux.push_back(a);
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        p->aux_join.push_back(ev);
+    }
+    if (e != cudaSuccess || p->aux.size() != p->aux_join.size()) {
+        free_aux(p);
+        return pcuda(e != cudaSuccess ? e : cudaErrorUnknown, "pool streams");
+    }
     set_error(SLBM_OK, "");
     return SLBM_OK;
 }
@@ -725,6 +912,9 @@ slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise) {
 void slbm_pool_free(slbm_pool_t *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (cudaStream_t a : p->aux) cudaStreamSynchronize(a);
+    free_aux(p);
+    if (p->fork) cudaEventDestroy(p->fork);
     drop_pool_graphs(p);
     if (p->d_tab) cudaFree(p->d_tab);
     if (p->d_hdr) cudaFree(p->d_hdr);

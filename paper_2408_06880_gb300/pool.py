@@ -73,5 +73,16 @@ class Pool:
         inside the pool's launch sequence; 0 batches every member."""
         A.check(A.lib().slbm_pool_set_split(self.h, int(split_cells)))
 
+    def set_group_bytes(self, nbytes: int):
+        """Batched members run in groups of at most nbytes of state + index,
+        each group all k steps of a `step(k)` before the next (L2 reuse);
+        0 = one group."""
+        A.check(A.lib().slbm_pool_set_group_bytes(self.h, int(nbytes)))
+
+    def set_streams(self, n: int):
+        """Graph steps spread the large members over n streams (forked from
+        and joined into the pool's stream); 1 = all in order."""
+        A.check(A.lib().slbm_pool_set_streams(self.h, int(n)))
+
     def abort(self, raise_flag: bool = True):
         A.check(A.lib().slbm_pool_abort(self.h, int(bool(raise_flag))))

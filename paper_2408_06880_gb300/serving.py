@@ -41,6 +41,14 @@ class Request:
     max_steps: int = 20000
     tol: float = 1e-6
     meta: dict = field(default_factory=dict)
+    _nf: int | None = field(default=None, repr=False, compare=False)
+
+    @property
+    def n_fluid(self) -> int:
+        """Fluid voxels of the geometry (counted once)."""
+        if self._nf is None:
+            self._nf = int(np.count_nonzero(self.flags == 0))
+        return self._nf
 
 
 @dataclass
@@ -69,7 +77,8 @@ class GpuExecutor:
     one `Pool`."""
 
     def __init__(self, q: int = 19, storage: int = A.FP32, capacity: int = 64, scale_exp: int | None = None,
-                 graph: bool = True, stream=None, pool_launch: tuple | None = None):
+                 graph: bool = True, stream=None, pool_launch: tuple | None = None,
+                 group_bytes: int | None = None, streams: int = 2):
         from .domain import Domain, auto_scale_exp
         from .pool import Pool
         self._Domain = Domain
@@ -79,12 +88,16 @@ class GpuExecutor:
         self.pool = Pool(q, storage, capacity, stream=stream)
         if pool_launch:
             self.pool.set_launch(*pool_launch)
+        if group_bytes is not None:
+            self.pool.set_group_bytes(group_bytes)
+        if streams > 1:
+            self.pool.set_streams(streams)
         self.capacity = capacity
 
     def footprint(self, req: Request) -> int:
         """Device bytes a request will hold (PDF-list, index-list, cell list,
         reduction partials), from its fluid-cell count."""
-        nf = int(np.count_nonzero(req.flags == 0))
+        nf = req.n_fluid
         S = (nf + 127) // 128 * 128
         b = 4 if self.storage == A.FP32 else 2
         return self.q * S * b + (self.q - 1) * S * 4 + nf * 4 + ((nf + 2047) // 2048) * 40 + 1024
@@ -136,10 +149,12 @@ class Server:
         used = 0
         busy_s = 0.0
         updates = 0
-        while queue or active:
+
+        def admit(fresh: bool) -> None:
+            """FIFO admission with bounded lookahead, by slot and budget.
+            fresh: a chunk is in flight that the new requests are not part of."""
+            nonlocal used
             now = self.clock() - t0
-            # ---- admission: FIFO with bounded lookahead, by slot and budget
-            admitted_any = False
             i = 0
             while i < min(len(queue), self.lookahead) and len(active) < self.ex.capacity:
                 req = queue[i]
@@ -164,11 +179,16 @@ class Server:
                     results.append(Result(req.rid, None, 0, False, req.arrival, None, self.clock() - t0,
                                           error=f"open failed: {e}"))
                     continue
-                active[slot] = dict(req=req, dom=dom, need=need, steps=0, prev=None,
-                                    t_admit=self.clock() - t0, n=int(req.flags.size),
-                                    nf=int(np.count_nonzero(req.flags == 0)))
+                active[slot] = dict(req=req, dom=dom, need=need, steps=0, prev=None, fresh=fresh,
+                                    t_admit=self.clock() - t0, n=int(req.flags.size), nf=req.n_fluid)
                 used += need
-                admitted_any = True
+
+        while queue or active:
+            # Requests are opened while a chunk runs on the device (below);
+            # here only when nothing runs, or when arrivals are timed and a
+            # newcomer should not wait for the next chunk.
+            if not active or realtime:
+                admit(False)
             if not active:
                 if queue and realtime:
                     wait = queue[0].arrival - (self.clock() - t0)
@@ -181,6 +201,7 @@ class Server:
                 if self.fault_hook:
                     self.fault_hook("step", None)
                 self.ex.step(self.chunk)
+                admit(True)                   # overlaps the chunk in flight
                 sums = self.ex.sums()
             except A.SlbmError as e:
                 # a device-level failure ends every active request
@@ -191,6 +212,9 @@ class Server:
                 continue
             busy_s += self.clock() - tb
             for slot, st in list(active.items()):
+                if st["fresh"]:               # joined after this chunk was launched
+                    st["fresh"] = False
+                    continue
                 st["steps"] += self.chunk
                 updates += st["nf"] * self.chunk
                 s = sums[slot]
@@ -242,6 +266,7 @@ class Server:
         return {"requests": len(results), "solved": len(ok), "failed": len(results) - len(ok),
                 "wall_s": wall, "solves_per_s": len(ok) / wall if wall > 0 else math.nan,
                 "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "latency_mean_s": float(np.mean(lat)),
                 "mflups": updates / wall / 1e6 if wall > 0 else math.nan, "device_busy_s": busy_s,
                 "converged": sum(r.converged for r in ok)}
 

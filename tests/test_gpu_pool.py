@@ -37,18 +37,32 @@ def _alone(g, kw, steps):
         return d.get_state()[0], d.reduce()
 
 
-@pytest.mark.parametrize("split", [0, 10000])
+# (split, group bytes, streams): split 10000 -- the larger members step with
+# their own kernels, the smaller ones share the batched launch; group 0 -- one
+# group of all batched members per launch; group 1 -- every member a group of
+# its own, all k steps of it before the next; None -- the default grouping;
+# streams 3 -- graph steps spread the large members over three streams
+SPLIT_GROUP = [(0, 0, 1), (0, 1, 1), (10000, 1, 1), (10000, None, 1), (10000, None, 3), (0, None, 2)]
+
+
+def _configure(pool, split, group, streams=1):
+    pool.set_split(split)
+    if group is not None:
+        pool.set_group_bytes(group)
+    if streams > 1:
+        pool.set_streams(streams)
+
+
+@pytest.mark.parametrize("split,group,streams", SPLIT_GROUP)
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
 @pytest.mark.parametrize("graph", [False, True])
-def test_pool_members_match_alone_bitwise(storage, graph, split):
-    # split 10000: the larger members step with their own kernels, the
-    # smaller ones share the batched launch
+def test_pool_members_match_alone_bitwise(storage, graph, split, group, streams):
     cases = _cases(storage)
     steps = 9
     want = [_alone(g, kw, steps) for g, kw in cases]
     doms = [gpu_domain(g, **kw) for g, kw in cases]
     with P.Pool(19, storage, capacity=8) as pool:
-        pool.set_split(split)
+        _configure(pool, split, group, streams)
         slots = [pool.add(d) for d in doms]
         pool.step(4, graph=graph)
         pool.step(5, graph=graph)
@@ -64,14 +78,14 @@ def test_pool_members_match_alone_bitwise(storage, graph, split):
         d.close()
 
 
-@pytest.mark.parametrize("split", [0, 10000])
-def test_mixed_parities_and_membership_changes_under_graph_replay(split):
+@pytest.mark.parametrize("split,group,streams", SPLIT_GROUP)
+def test_mixed_parities_and_membership_changes_under_graph_replay(split, group, streams):
     cases = _cases()
     (ga, ka), (gb, kb), (gc, kc), _ = cases
     a, b, c = gpu_domain(ga, **ka), gpu_domain(gb, **kb), gpu_domain(gc, **kc)
     a.step(3)                                  # a joins at odd parity
     with P.Pool(19, 0, capacity=4) as pool:
-        pool.set_split(split)
+        _configure(pool, split, group, streams)
         sa, sb = pool.add(a), pool.add(b)
         pool.step(4, graph=True)               # a: 7, b: 4
         pool.remove(sa)
@@ -79,7 +93,10 @@ def test_mixed_parities_and_membership_changes_under_graph_replay(split):
         pool.step(4, graph=True)               # b: 8, c: 4
         pool.step(1, graph=False)              # b: 9, c: 5
         pool.reduce()
-        for d, (g, kw), n in ((a, (ga, ka), 7), (b, (gb, kb), 9), (c, (gc, kc), 5)):
+        pool.remove(sb)                        # with split 10000 b steps alone: the
+        pool.step(2, graph=True)               # batched table stays as it was; c: 7
+        pool.reduce()
+        for d, (g, kw), n in ((a, (ga, ka), 7), (b, (gb, kb), 9), (c, (gc, kc), 7)):
             got, step = d.get_state()
             want, _ = _alone(g, kw, n)
             assert step == n and np.array_equal(got, want)
