@@ -61,7 +61,7 @@ typedef enum {
 
 enum { SLBM_SRT = 0, SLBM_TRT = 1 };
 enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
-enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1 };
+enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1, SLBM_LAYOUT_SPARSE_PULL = 2 };
 enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
 enum { SLBM_ORDER_CELLS = 0, SLBM_ORDER_VOXELS = 1 };
 
@@ -80,9 +80,24 @@ typedef struct {
     double rho_out;            /* pressure-outlet density */
     int32_t storage;           /* SLBM_FP32 / SLBM_FP16 / SLBM_BF16 shifted populations */
     int32_t scale_exp;         /* FP16/BF16: stored value = (f_i - w_i) * 2^scale_exp, |.| <= 40 */
-    int32_t layout;            /* SLBM_LAYOUT_SPARSE (the method) or SLBM_LAYOUT_DENSE (comparator) */
+    int32_t layout;            /* SLBM_LAYOUT_SPARSE (the method: one field, AA pattern),
+                                  SLBM_LAYOUT_DENSE (comparator) or SLBM_LAYOUT_SPARSE_PULL
+                                  (comparison scheme: the same lists, two fields, pull) */
     int32_t reserved;          /* must be 0 */
 } slbm_desc;
+
+/* SLBM_LAYOUT_SPARSE_PULL -- the two-grid pull scheme the paper compares the
+ * AA pattern with (Sec. 5.1, Table 2's pull row): the same compacted cells and
+ * canonical pull entries P(i,k), two PDF fields; each step gathers f_i from
+ * P(i,k) of one field, collides, and writes the cell's own column of the
+ * other (reads Q B_pdf + (Q-1) x 4 index bytes, writes Q B_pdf per cell).  At
+ * step 0 the field holds the natural populations; the first step collides in
+ * place, so the stored field at step t > 0 is the post-collision C(t-1), and
+ * read-outs (macroscopic, reduce) pull it through P.  Walls and periodic
+ * boundaries only (SLBM_EUNSUPPORTED with inlet/outlet voxels); one launch
+ * shape (set_launch: SLBM_EUNSUPPORTED); no pools, no link codes.
+ * get_state/set_state move the stored field of the current step.  Results are
+ * bit-identical to the AA layout's at every step. */
 
 /* Optional device allocator.  alloc returns device memory (256-byte aligned)
  * or NULL; free releases it.  Both are called on the creating thread only. */
@@ -158,6 +173,23 @@ slbm_status sparse_lbm_info(const slbm_t *h, slbm_info *out);
 slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_t *index_rows,
                                     int32_t *link_cell, int32_t *link_dir, int32_t *link_type);
 
+/* The 16-bit link codes the odd step reads (launch variant 4), to HOST
+ * memory: codes [(Q-1) x S] (uint16, row i-1 = direction i) and bases
+ * [(S/128) x (Q-1)] (int32, one column base per 128-cell tile and direction).
+ * They encode the device's odd-step slot R(i,k) -- the pull entry P(i,k) of
+ * Sec. 3.1 with its row flipped between i and inverse(i) -- in 2 bytes.  With
+ * b = bases[k/128][i-1]:
+ *   b == -1        : the tile-direction's fluid columns span 0xFFFE or
+ *                    more; R is read from the int32 list (codes 0xFFFE)
+ *   code == 0xFFFE : inlet/outlet link; R is read from the int32 list
+ *   code == 0xFFFF : wall (the cell's own slot, R = i*S + k) or padding
+ *   otherwise      : fluid neighbour, R = inverse(i)*S + b + code
+ * The paper stores 4-byte indices; this encoding is an addition of this
+ * library (it halves the index bytes of the odd step).  Builds the codes on
+ * first use (as launch variant 4 does).  Either pointer may be NULL.
+ * Synchronous.  Sparse layout only. */
+slbm_status sparse_lbm_export_codes(slbm_t *h, uint16_t *codes, int32_t *bases);
+
 /* Checkpoint / resume: raw stored PDFs (Q x S elements of the storage type,
  * bytes = Q*S*element size) plus the step counter, to or from HOST memory.
  * A resumed run continues bit-for-bit like an uninterrupted one. */
@@ -178,7 +210,13 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
  *            that will run one residency wave later;
  * variant 3: as variant 2, but each thread re-reads its slots from the list
  *            before the scatter instead of keeping them in registers (domains
- *            without inlet/outlet links; others run variant 2).
+ *            without inlet/outlet links; others run variant 2);
+ * variant 4: odd step only, as variant 2 (1 or 2 cells per thread), with the
+ *            slots read as 16-bit link codes (sparse_lbm_export_codes) and
+ *            the L2 prefetch of the codes: 2 instead of 4 index bytes per
+ *            link.  The codes ((Q-1) x S x 2 bytes) are built and allocated
+ *            on the first selection of this variant (SLBM_ENOMEM if the
+ *            allocation fails).
  * Defaults: even variant 0, 64 x 2 (FP16: variant 1, 128 x 2); odd variant 2,
  * 128 x 1.  Results are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);

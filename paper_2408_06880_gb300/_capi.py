@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libsparse_lbm.so")
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EDIVERGED, ETIMEOUT, EABORTED, EDEVICE = range(9)
 SRT, TRT = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
-SPARSE, DENSE = 0, 1
+SPARSE, DENSE, SPARSE_PULL = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 ORDER_CELLS, ORDER_VOXELS = 0, 1
 NOALLOC_MAX_VOXELS = 268435456
@@ -62,6 +62,7 @@ SIGNATURES = {
     "sparse_lbm_init_equilibrium": (_st, [_vp, _vp, _vp, _i32, _i32]),
     "sparse_lbm_info": (_st, [_vp, C.POINTER(Info)]),
     "sparse_lbm_export_lists": (_st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sparse_lbm_export_codes": (_st, [_vp, _vp, _vp]),
     "sparse_lbm_state_bytes": (_st, [_vp, C.POINTER(_i64)]),
     "sparse_lbm_get_state": (_st, [_vp, _vp, C.POINTER(_i64)]),
     "sparse_lbm_set_state": (_st, [_vp, _vp, _i64]),

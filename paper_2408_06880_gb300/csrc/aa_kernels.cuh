@@ -158,12 +158,6 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
     if (err) atomicCAS(err, 0, code);
 }
 
-// pf_dist > 0 (CPT = 1 only): thread 0 first asks the bulk-copy engine to
-// prefetch into L2 the index-list rows of the CTA pf_dist blocks ahead -- about
-// one residency wave later -- so that CTA's first round trip hits L2.
-// RELOAD (CPT = 1, no links): the slots are re-read from the list (an L1
-// hit) before the scatter instead of being held in registers through the
-// collision, which frees registers for more resident threads.
 // CPT cells per thread, strided by the block size (cell c of thread t in block
 // b is b*blockDim*CPT + c*blockDim + t), so that every load and store
 // instruction of a warp covers consecutive cells.
@@ -173,11 +167,16 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // RELOAD (CPT = 1, no links): the slots are re-read from the list (an L1
 // hit) before the scatter instead of being held in registers through the
 // collision, which frees registers for more resident threads.
-template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false>
+// CODE: the slots come from the 16-bit link codes and their per-tile column
+// bases (2 bytes per link instead of 4); an escape code reads the slot from
+// the int32 list.  The decoded slot equals R(i, k) exactly.
+template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false>
 __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                      const int32_t *__restrict__ P, int32_t S, int32_t nf,
                                                      const LinkMap *__restrict__ maps, int32_t n_links,
-                                                     CollideParams p, int32_t *err, int32_t pf_dist) {
+                                                     CollideParams p, int32_t *err, int32_t pf_dist,
+                                                     const uint16_t *__restrict__ code = nullptr,
+                                                     const int32_t *__restrict__ cbase = nullptr) {
     using St = Store<ST>;
     using T = typename St::T;
     const int32_t span = blockDim.x * CPT;
@@ -185,24 +184,65 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
         const int64_t c0 = ((int64_t)blockIdx.x + pf_dist) * span;
         if (c0 < nf) {
             const int64_t left = (int64_t)S - c0;
-            const uint32_t bytes = (uint32_t)(left < (int64_t)span ? left : (int64_t)span) * 4u;
+            const uint32_t cells = (uint32_t)(left < (int64_t)span ? left : (int64_t)span);
 #pragma unroll
-            for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(P + r * S + c0, bytes);
+            for (int r = 0; r < Q - 1; ++r) {
+                if (CODE) bulk_prefetch_l2(code + r * S + c0, cells * 2u);
+                else bulk_prefetch_l2(P + r * S + c0, cells * 4u);
+            }
         }
     }
     const int32_t kb = blockIdx.x * span + threadIdx.x;
-    if (kb >= nf) return;
+    // CODE: every lane stays to the end of the decode (warp shuffles)
+    if (!CODE && kb >= nf) return;
     int32_t e[CPT][Q];
     bool valid[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) valid[c] = kb + c * (int32_t)blockDim.x < nf;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
+    if (CODE) {
+        // A warp's cells lie in one code tile: lane r holds the tile's base of
+        // direction r+1, loaded beside the codes and broadcast by shuffles.
+        // Base -1 (a tile-direction of too wide a span): the whole warp reads
+        // the int32 slots; an escape code (inlet/outlet link, domains with
+        // links only) reads that one slot.
+        const int lane = threadIdx.x & 31;
+        const int32_t n_tiles = S / CODE_TILE;
+        uint32_t cc[CPT][Q];
+        int32_t bl[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-            const int32_t k = kb + c * blockDim.x;
-            if (RELOAD) e[c][i] = P[(i - 1) * S + k];
-            else e[c][i] = valid[c] ? __ldcs(P + (i - 1) * S + k) : 0;
+            const int32_t tile = (kb + c * (int32_t)blockDim.x) / CODE_TILE;
+            bl[c] = (lane < Q - 1 && tile < n_tiles) ? __ldg(cbase + tile * (Q - 1) + lane) : -1;
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int32_t k = kb + c * blockDim.x;
+                cc[c][i] = valid[c] ? __ldcs(code + (i - 1) * S + k) : CODE_WALL;
+            }
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int32_t k = kb + c * blockDim.x;
+                const int32_t b = __shfl_sync(0xffffffffu, bl[c], i - 1);
+                const uint32_t x = cc[c][i];
+                if (b >= 0 && !(HAS_BC && x == CODE_ESCAPE)) e[c][i] = x == CODE_WALL ? i * S + k : inv(i) * S + b + (int32_t)x;
+                else e[c][i] = valid[c] ? P[(i - 1) * S + k] : i * S + k;
+            }
+        }
+        if (kb >= nf) return;
+    } else {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int32_t k = kb + c * blockDim.x;
+                if (RELOAD) e[c][i] = P[(i - 1) * S + k];
+                else e[c][i] = valid[c] ? __ldcs(P + (i - 1) * S + k) : 0;
+            }
         }
     }
     float g[CPT][Q];

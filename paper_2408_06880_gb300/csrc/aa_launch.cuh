@@ -129,15 +129,26 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const bool bc = nl > 0;
     if (d.checked) {
-        if (bc) aa_odd_kernel<Q, ST, 1, true, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0);
-        else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0);
+        if (bc) aa_odd_kernel<Q, ST, 1, true, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0, nullptr, nullptr);
+        else aa_odd_kernel<Q, ST, 1, false, true><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0, nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    // variant 4: slots from the 16-bit link codes, with the L2 prefetch of the codes
+    if (sh.variant == 4) {
+        const uint16_t *code = reinterpret_cast<const uint16_t *>(d.code.p);
+        const int32_t *cb = reinterpret_cast<const int32_t *>(d.code_base.p);
+        auto kc = sh.cells == 1
+                      ? (bc ? aa_odd_kernel<Q, ST, 1, true, false, false, true> : aa_odd_kernel<Q, ST, 1, false, false, false, true>)
+                      : (bc ? aa_odd_kernel<Q, ST, 2, true, false, false, true> : aa_odd_kernel<Q, ST, 2, false, false, false, true>);
+        const int32_t pfc = (int32_t)persistent_grid(kc, sh.threads, INT32_MAX);
+        kc<<<grid(sh.cells), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfc, code, cb);
         return cudaGetLastError();
     }
     // variant 3: slots re-read before the scatter (no links), with the L2 prefetch
     if (sh.variant == 3 && !bc) {
         auto kr = aa_odd_kernel<Q, ST, 1, false, false, true>;
         const int32_t pfr = (int32_t)persistent_grid(kr, sh.threads, INT32_MAX);
-        kr<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfr);
+        kr<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfr, nullptr, nullptr);
         return cudaGetLastError();
     }
     // variant 2: L2 prefetch of the index rows one residency wave ahead
@@ -148,10 +159,10 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
         pf = (int32_t)persistent_grid(kp, sh.threads, INT32_MAX);
     }
     switch (sh.cells * 2 + (bc ? 1 : 0)) {
-        case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
-        case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
-        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
-        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf); break;
+        case 2: aa_odd_kernel<Q, ST, 1, false, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr); break;
+        case 3: aa_odd_kernel<Q, ST, 1, true, false><<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr); break;
+        case 4: aa_odd_kernel<Q, ST, 2, false, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr); break;
+        case 5: aa_odd_kernel<Q, ST, 2, true, false><<<grid(2), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -112,21 +112,24 @@ cudaError_t launch_bc_fixup(const Domain &d, int post, cudaStream_t st) {
     return d.q == 19 ? launch_bc_fixup_q<19>(d, post, st) : launch_bc_fixup_q<27>(d, post, st);
 }
 
-static cudaError_t launch_one_step(const Domain &d, int parity, cudaStream_t st) {
-    return d.layout == SLBM_LAYOUT_SPARSE ? launch_aa_step(d, parity, st) : launch_dense_step(d, parity, st);
+// Step t -> t+1 (t = absolute step index).
+static cudaError_t launch_one_step(const Domain &d, int64_t t, cudaStream_t st) {
+    if (d.pull()) return launch_pull_step(d, t, st);
+    return d.layout == SLBM_LAYOUT_SPARSE ? launch_aa_step(d, (int)(t & 1), st) : launch_dense_step(d, (int)(t & 1), st);
 }
 
-// The domain's cached graph of n steps from its current parity, captured on
-// first use (capture records launches only; it runs nothing).
+// The domain's cached graph of n steps from its current parity (pull layout:
+// a separate one from step 0, whose first launch collides in place),
+// captured on first use (capture records launches only; it runs nothing).
 cudaError_t domain_graph(Domain &d, int32_t n, cudaGraphExec_t *out) {
-    const std::pair<int, int> key(n, (int)(d.step & 1));
+    const std::pair<int, int> key(n, (d.pull() && d.step == 0) ? 2 : (int)(d.step & 1));
     auto it = d.graphs.find(key);
     if (it == d.graphs.end()) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
         cudaError_t le = cudaSuccess;
-        for (int32_t t = 0; t < n && le == cudaSuccess; ++t) le = launch_one_step(d, (int)((d.step + t) & 1), d.stream);
+        for (int32_t t = 0; t < n && le == cudaSuccess; ++t) le = launch_one_step(d, d.step + t, d.stream);
         e = cudaStreamEndCapture(d.stream, &g);
         if (le != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -150,9 +153,9 @@ static void drop_graphs(Domain &d) {
 
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
-    DevBuf *bufs[] = {&d.pdf,  &d.P,      &d.cell_voxel, &d.link_cell,   &d.link_dir, &d.link_type,
-                      &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask, &d.red_partial,
-                      &d.red_out, &d.err};
+    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.cell_voxel, &d.link_cell,
+                      &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask,
+                      &d.red_partial, &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
 }
 
@@ -165,6 +168,19 @@ static slbm_status ok() {
 static slbm_status err(slbm_status s, const std::string &m) {
     set_error(s, m);
     return s;
+}
+
+// Build the 16-bit link codes on first use (sparse layout only).
+static slbm_status ensure_codes(Domain &d) {
+    if (d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "link codes exist for the sparse layout only");
+    if (d.code.p || d.S == 0) return SLBM_OK;
+    Ctx cx = d.ctx();
+    if (build_link_codes(cx, d) || cx.check(cudaStreamSynchronize(d.stream), "build codes")) {
+        cx.release(d.code);
+        cx.release(d.code_base);
+        return cx.status == SLBM_OK ? err(SLBM_ECUDA, g_msg) : cx.status;
+    }
+    return SLBM_OK;
 }
 
 static slbm_status cuda_err(cudaError_t e, const char *what) {
@@ -195,7 +211,8 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
         return err(SLBM_EINVAL, "trt_magic must be > 0");
     if (s.storage < SLBM_FP32 || s.storage > SLBM_BF16) return err(SLBM_EINVAL, "storage must be 0, 1 or 2");
     if (s.scale_exp < -40 || s.scale_exp > 40) return err(SLBM_EINVAL, "scale_exp must lie in [-40, 40]");
-    if (s.layout != SLBM_LAYOUT_SPARSE && s.layout != SLBM_LAYOUT_DENSE) return err(SLBM_EINVAL, "bad layout");
+    if (s.layout != SLBM_LAYOUT_SPARSE && s.layout != SLBM_LAYOUT_DENSE && s.layout != SLBM_LAYOUT_SPARSE_PULL)
+        return err(SLBM_EINVAL, "bad layout");
     if (s.reserved != 0) return err(SLBM_EINVAL, "reserved must be 0");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(s.force[a])) return err(SLBM_EINVAL, "force must be finite");
@@ -214,6 +231,8 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
         return err(SLBM_EINVAL, "n_inlet_u must equal the number of inlet voxels");
     if (s.layout == SLBM_LAYOUT_DENSE && has_bc)
         return err(SLBM_EUNSUPPORTED, "the dense comparator supports walls and periodic boundaries only");
+    if (s.layout == SLBM_LAYOUT_SPARSE_PULL && has_bc)
+        return err(SLBM_EUNSUPPORTED, "the pull layout supports walls and periodic boundaries only");
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
     if (ce != cudaSuccess || ndev == 0) {
@@ -262,11 +281,23 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     int rc = cx.alloc(flags, N);
     if (!rc) rc = cx.check(cudaMemcpyAsync(flags.p, s.flags, N, cudaMemcpyHostToDevice, d.stream), "flags H2D");
     if (!rc) {
-        if (d.layout == SLBM_LAYOUT_SPARSE) {
+        if (d.sparse()) {
             rc = build_sparse_lists(cx, d, (const uint8_t *)flags.p, has_bc, s.inlet_u, s.n_inlet_u);
             if (!rc && d.n_fluid != n_fluid_host) {
                 cx.fail(SLBM_ECUDA, "device compaction count disagrees with the host count");
                 rc = -1;
+            }
+            if (!rc && d.pull() && d.S > 0) {   // the pull step reads the canonical entries P(i,k)
+                DevBuf canon;
+                rc = cx.alloc(canon, (int64_t)(d.q - 1) * d.S * 4);
+                if (!rc) rc = cx.check(launch_unflip(d, (int32_t *)canon.p, d.stream), "unflip");
+                if (!rc) rc = cx.check(cudaStreamSynchronize(d.stream), "unflip sync");
+                if (!rc) {
+                    cx.release(d.P);
+                    d.P = canon;
+                } else {
+                    cx.release(canon);
+                }
             }
         } else {
             d.n_fluid = n_fluid_host;
@@ -277,6 +308,8 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     const int64_t rows_bytes = (int64_t)d.q * d.S * d.bytes_per_pdf();
     if (!rc) rc = cx.alloc(d.pdf, rows_bytes);
     if (!rc && rows_bytes) rc = cx.check(cudaMemsetAsync(d.pdf.p, 0, rows_bytes, d.stream), "memset pdf");
+    if (!rc && d.pull()) rc = cx.alloc(d.pdf2, rows_bytes);
+    if (!rc && d.pull() && rows_bytes) rc = cx.check(cudaMemsetAsync(d.pdf2.p, 0, rows_bytes, d.stream), "memset pdf2");
     if (!rc) rc = cx.alloc(d.red_partial, std::max<int64_t>(d.red_chunks(), 1) * 5 * sizeof(double));
     if (!rc) rc = cx.alloc(d.red_out, 5 * sizeof(double));
     if (!rc) rc = cx.alloc(d.err, sizeof(int32_t));
@@ -299,7 +332,7 @@ slbm_status sparse_lbm_step(slbm_t *h, int32_t n) {
     if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
     Domain &d = h->d;
     for (int32_t t = 0; t < n; ++t) {
-        const cudaError_t e = launch_one_step(d, (int)(d.step & 1), d.stream);
+        const cudaError_t e = launch_one_step(d, d.step, d.stream);
         if (e != cudaSuccess) return cuda_err(e, "step launch");
         ++d.step;
     }
@@ -324,7 +357,7 @@ slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t orde
     if (order != SLBM_ORDER_CELLS && order != SLBM_ORDER_VOXELS) return err(SLBM_EINVAL, "bad order");
     if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return err(SLBM_EINVAL, "bad mem");
     Domain &d = h->d;
-    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox);
+    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.sparse() ? d.n_fluid : d.n_vox);
     if (mem == SLBM_MEM_DEVICE) {
         if (order == SLBM_ORDER_VOXELS) {   // zero the non-fluid entries first
             if (rho && n) cudaMemsetAsync(rho, 0, n * sizeof(float), d.stream);
@@ -373,7 +406,7 @@ slbm_status sparse_lbm_init_equilibrium(slbm_t *h, const float *rho, const float
     if (!h) return err(SLBM_EINVAL, "null handle");
     if (order != SLBM_ORDER_CELLS && order != SLBM_ORDER_VOXELS) return err(SLBM_EINVAL, "bad order");
     Domain &d = h->d;
-    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox);
+    const int64_t n = order == SLBM_ORDER_VOXELS ? d.n_vox : (d.sparse() ? d.n_fluid : d.n_vox);
     Ctx cx = d.ctx();
     cx.held = nullptr;
     DevBuf dr, du;
@@ -424,7 +457,7 @@ slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_
                                     int32_t *link_dir, int32_t *link_type) {
     if (!h) return err(SLBM_EINVAL, "null handle");
     const Domain &d = h->d;
-    if (d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "lists exist for the sparse layout only");
+    if (!d.sparse()) return err(SLBM_EUNSUPPORTED, "lists exist for the sparse layouts only");
     cudaError_t e = cudaSuccess;
     auto cp = [&](void *dst, const void *src, int64_t bytes) {
         if (dst && bytes > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, d.stream);
@@ -435,9 +468,13 @@ slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_
     cx.held = nullptr;
     DevBuf tmp;
     if (index_rows && pbytes > 0) {
-        if (cx.alloc(tmp, pbytes)) return err(cx.status, g_msg);
-        e = launch_unflip(d, (int32_t *)tmp.p, d.stream);
-        cp(index_rows, tmp.p, pbytes);
+        if (d.pull()) {                 // stored canonical
+            cp(index_rows, d.P.p, pbytes);
+        } else {
+            if (cx.alloc(tmp, pbytes)) return err(cx.status, g_msg);
+            e = launch_unflip(d, (int32_t *)tmp.p, d.stream);
+            cp(index_rows, tmp.p, pbytes);
+        }
     }
     cp(link_cell, d.link_cell.p, d.n_links * 4);
     cp(link_dir, d.link_dir.p, d.n_links * 4);
@@ -445,6 +482,20 @@ slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_
     if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
     cx.release(tmp);
     return e == cudaSuccess ? ok() : cuda_err(e, "export lists");
+}
+
+slbm_status sparse_lbm_export_codes(slbm_t *h, uint16_t *codes, int32_t *bases) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    const slbm_status st = ensure_codes(h->d);
+    if (st != SLBM_OK) return st;
+    const Domain &d = h->d;
+    cudaError_t e = cudaSuccess;
+    const int64_t cbytes = (int64_t)(d.q - 1) * d.S * 2, bbytes = d.S / CODE_TILE * (d.q - 1) * 4;
+    if (codes && cbytes > 0) e = cudaMemcpyAsync(codes, d.code.p, cbytes, cudaMemcpyDeviceToHost, d.stream);
+    if (bases && bbytes > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(bases, d.code_base.p, bbytes, cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    return e == cudaSuccess ? ok() : cuda_err(e, "export codes");
 }
 
 slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes) {
@@ -458,7 +509,7 @@ slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step) {
     const Domain &d = h->d;
     const int64_t b = (int64_t)d.q * d.S * d.bytes_per_pdf();
     cudaError_t e = cudaSuccess;
-    if (b) e = cudaMemcpyAsync(host, d.pdf.p, b, cudaMemcpyDeviceToHost, d.stream);
+    if (b) e = cudaMemcpyAsync(host, d.cur_pdf(), b, cudaMemcpyDeviceToHost, d.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
     if (e != cudaSuccess) return cuda_err(e, "get_state");
     if (step) *step = d.step;
@@ -470,7 +521,11 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step) {
     Domain &d = h->d;
     const int64_t b = (int64_t)d.q * d.S * d.bytes_per_pdf();
     cudaError_t e = cudaSuccess;
-    if (b) e = cudaMemcpyAsync(d.pdf.p, host, b, cudaMemcpyHostToDevice, d.stream);
+    const int64_t was = d.step;
+    d.step = step;
+    void *dst = d.cur_pdf();           // the grid that holds the state at `step`
+    d.step = was;
+    if (b) e = cudaMemcpyAsync(dst, host, b, cudaMemcpyHostToDevice, d.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
     if (e != cudaSuccess) return cuda_err(e, "set_state");
     d.step = step;
@@ -479,6 +534,7 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step) {
 
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
+    if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
     if (variant == 0) {
         if (threads < 32 || threads > 256 || threads % 32)
             return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");
@@ -489,12 +545,16 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variant covers sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
-    } else if (variant == 2 || variant == 3) {
-        if (parity != 1 || threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant == 2 && cells == 2)))
-            return err(SLBM_EINVAL, "variants 2 and 3 are for the odd step: threads 32..256 (multiple of 32), "
-                                    "cells 1 (variant 2 also 2)");
+    } else if (variant >= 2 && variant <= 4) {
+        if (parity != 1 || threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant != 3 && cells == 2)))
+            return err(SLBM_EINVAL, "variants 2..4 are for the odd step: threads 32..256 (multiple of 32), "
+                                    "cells 1 (variants 2 and 4 also 2)");
+        if (variant == 4) {
+            const slbm_status st = ensure_codes(h->d);
+            if (st != SLBM_OK) return st;
+        }
     } else {
-        return err(SLBM_EINVAL, "variant must be 0, 1, 2 or 3");
+        return err(SLBM_EINVAL, "variant must be 0..4");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);

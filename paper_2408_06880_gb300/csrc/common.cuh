@@ -35,6 +35,11 @@ __host__ __device__ __forceinline__ constexpr int cz(int i) {
                            1, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, 1, -1};
     return t[i];
 }
+// 16-bit link codes of the odd-step slots: cells per tile of one column
+// base, and the two reserved codes (own slot; read the int32 slot instead).
+constexpr int32_t CODE_TILE = 128;
+constexpr uint32_t CODE_WALL = 0xFFFF, CODE_ESCAPE = 0xFFFE;
+
 __host__ __device__ __forceinline__ constexpr int inv(int i) {
     return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
 }

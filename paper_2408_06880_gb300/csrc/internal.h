@@ -54,7 +54,10 @@ struct Domain {
     int64_t n_fluid = 0, S = 0, n_links = 0, step = 0;
     // device data
     DevBuf pdf;                        // Q x S stored populations
+    DevBuf pdf2;                       // second grid (pull layout only)
     DevBuf P;                          // (Q-1) x S odd-step slots R(i,k) (row-flipped pull entries)
+    DevBuf code;                       // (Q-1) x S 16-bit link codes of R (sparse)
+    DevBuf code_base;                  // (S / CODE_TILE) x (Q-1) column bases of the codes
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity
@@ -74,6 +77,10 @@ struct Domain {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, parity) -> exec
 
     int bytes_per_pdf() const { return storage == SLBM_FP32 ? 4 : 2; }
+    bool sparse() const { return layout != SLBM_LAYOUT_DENSE; }      // compacted cell lists
+    bool pull() const { return layout == SLBM_LAYOUT_SPARSE_PULL; }
+    // grid holding the current state (pull: A at t = 0 and odd t, else B)
+    void *cur_pdf() const { return (pull() && step > 0 && !(step & 1)) ? pdf2.p : pdf.p; }
     int64_t red_chunks() const;
     CollideParams collide_params() const;
     Ctx ctx() {
@@ -92,10 +99,14 @@ constexpr int RED_CHUNK = RED_THREADS * RED_CELLS_PER_THREAD;
 
 // lists.cu
 cudaError_t launch_unflip(const Domain &d, int32_t *out, cudaStream_t st);
+// 16-bit link codes of the odd-step slots (after build_sparse_lists)
+int build_link_codes(Ctx &cx, Domain &d);
 int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
                        int64_t n_inlet_u);
 // aa_q19.cu / aa_q27.cu (dispatch in api.cu)
 cudaError_t launch_aa_step(const Domain &d, int parity, cudaStream_t st);
+// pull.cu: one two-grid pull step from step index d.step + t
+cudaError_t launch_pull_step(const Domain &d, int64_t t, cudaStream_t st);
 // boundary fix-up before (post = 0) / after (post = 1) an even step
 cudaError_t launch_bc_fixup(const Domain &d, int post, cudaStream_t st);
 // The domain's cached CUDA graph of n steps from its current parity (captured

@@ -402,6 +402,77 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
     return 0;
 }
 
+// ------------------------------------------------------------- link codes
+// 16-bit form of the odd-step slots R(i, k).  A fluid neighbour's slot lies in
+// row inverse(i), so only its column needs storing; within a tile of
+// CODE_TILE consecutive cells the columns of one direction span little more
+// than the tile (neighbours of consecutive cells are near-consecutive in the
+// compacted order), so they are stored relative to the tile's smallest one:
+//   code = column - base       fluid neighbour
+//   code = CODE_WALL           wall: the cell's own slot i*S + k (and padding)
+//   code = CODE_ESCAPE         inlet/outlet link: read R(i, k) itself
+// base[tile * (Q-1) + i-1] is the smallest fluid column (0 if none), or -1
+// when the tile-direction's columns span CODE_ESCAPE or more (e.g. across a
+// periodic wrap): then every slot of the tile-direction is read from R
+// itself and its codes are CODE_ESCAPE.  One CTA per tile; the span is
+// reduced in a fixed order, so the codes are deterministic.
+template <int Q>
+__global__ void __launch_bounds__(CODE_TILE) build_codes_kernel(const int32_t *__restrict__ R, int32_t S, int32_t nf,
+                                                                uint16_t *__restrict__ code,
+                                                                int32_t *__restrict__ base) {
+    constexpr int W = CODE_TILE / 32;
+    __shared__ int32_t wlo[W], whi[W];
+    const int32_t k = blockIdx.x * CODE_TILE + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 1; i < Q; ++i) {
+        const int32_t e = k < nf ? R[(i - 1) * S + k] : 0;
+        const bool link = k < nf && e < 0;                    // inlet/outlet
+        const bool fluid = k < nf && e >= 0 && e / S != i;    // row inverse(i)
+        const int32_t col = fluid ? e - inv(i) * S : 0;
+        int32_t lo = fluid ? col : INT32_MAX, hi = fluid ? col : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            wlo[warp] = lo;
+            whi[warp] = hi;
+        }
+        __syncthreads();
+        lo = wlo[0];
+        hi = whi[0];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            lo = min(lo, wlo[w]);
+            hi = max(hi, whi[w]);
+        }
+        __syncthreads();                                  // wlo/whi are reused by the next direction
+        const bool wide = hi >= 0 && hi - lo >= (int32_t)CODE_ESCAPE;
+        const int32_t b = wide ? -1 : (hi < 0 ? 0 : lo);
+        uint16_t c = (uint16_t)CODE_WALL;                 // walls and padding
+        if (wide || link) c = (uint16_t)CODE_ESCAPE;
+        else if (fluid) c = (uint16_t)(col - b);          // below CODE_ESCAPE
+        code[(int64_t)(i - 1) * S + k] = c;
+        if (threadIdx.x == 0) base[(int64_t)blockIdx.x * (Q - 1) + (i - 1)] = b;
+    }
+}
+
+int build_link_codes(Ctx &cx, Domain &d) {
+    if (d.S == 0) return 0;
+    const int64_t tiles = d.S / CODE_TILE;
+    if (cx.alloc(d.code, (int64_t)(d.q - 1) * d.S * sizeof(uint16_t)) ||
+        cx.alloc(d.code_base, tiles * (d.q - 1) * sizeof(int32_t)))
+        return -1;
+    if (d.q == 19)
+        build_codes_kernel<19><<<(unsigned)tiles, CODE_TILE, 0, cx.stream>>>(
+            (const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid, (uint16_t *)d.code.p, (int32_t *)d.code_base.p);
+    else
+        build_codes_kernel<27><<<(unsigned)tiles, CODE_TILE, 0, cx.stream>>>(
+            (const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid, (uint16_t *)d.code.p, (int32_t *)d.code_base.p);
+    return cx.check(cudaGetLastError(), "build_codes launch");
+}
+
 }  // namespace slbm
 
 // ------------------------------------------------ allocation-free compaction

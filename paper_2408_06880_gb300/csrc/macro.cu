@@ -40,6 +40,25 @@ struct SparseView {
     }
 };
 
+// Pull layout: at t > 0 the stored grid holds the post-collision C(t-1), and
+// the natural populations are its pull through the canonical entries,
+// f_i(k) = C[P(i,k)] (no inlet/outlet links in this layout); at t = 0 the
+// grid is natural.
+struct PullView {
+    const int32_t *P;
+    const int32_t *cell_voxel;
+    int32_t S, n;
+    __device__ __forceinline__ bool fluid(int32_t) const { return true; }
+    __device__ __forceinline__ int32_t voxel(int32_t k) const { return cell_voxel[k]; }
+    template <int Q, class St>
+    __device__ __forceinline__ void load(const typename St::T *pdf, int32_t k, bool pulled, float inv_scale,
+                                         float (&g)[Q]) const {
+        g[0] = St::ld(pdf[k], inv_scale);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) g[i] = St::ld(pdf[pulled ? P[(i - 1) * S + k] : i * S + k], inv_scale);
+    }
+};
+
 // Dense comparator layout: every voxel is a column; the per-voxel mask holds
 // bit 31 = fluid and bit i = "pull neighbour of direction i is a wall".
 struct DenseView {
@@ -128,6 +147,10 @@ static cudaError_t with_types(const Domain &d, Fn &&fn) {
     auto by_view = [&](auto qtag, auto sttag) -> cudaError_t {
         constexpr int Q = decltype(qtag)::value;
         using St = Store<decltype(sttag)::value>;
+        if (d.pull()) {
+            PullView v{(const int32_t *)d.P.p, (const int32_t *)d.cell_voxel.p, (int32_t)d.S, (int32_t)d.n_fluid};
+            return fn(std::integral_constant<int, Q>{}, St{}, v);
+        }
         if (d.layout == SLBM_LAYOUT_SPARSE) {
             SparseView v{(const int32_t *)d.P.p, (const LinkMap *)d.link_map.p, (const int32_t *)d.cell_voxel.p,
                          (int32_t)d.S, (int32_t)d.n_fluid};
@@ -147,7 +170,7 @@ static cudaError_t with_types(const Domain &d, Fn &&fn) {
 }
 
 int64_t Domain::red_chunks() const {
-    const int64_t n = layout == SLBM_LAYOUT_SPARSE ? n_fluid : n_vox;
+    const int64_t n = sparse() ? n_fluid : n_vox;
     return (n + RED_CHUNK - 1) / RED_CHUNK;
 }
 
@@ -155,14 +178,14 @@ cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order,
     const int64_t chunks = d.red_chunks();
     if (chunks == 0) return cudaSuccess;
     const int64_t u_stride = order == SLBM_ORDER_VOXELS ? d.n_vox
-                                                        : (d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox);
-    const bool odd = d.step & 1;
+                                                        : (d.sparse() ? d.n_fluid : d.n_vox);
+    const bool odd = d.pull() ? d.step > 0 : (d.step & 1);
     const CollideParams p = d.collide_params();
     return with_types(d, [&](auto qtag, auto st_t, auto view) -> cudaError_t {
         constexpr int Q = decltype(qtag)::value;
         using St = decltype(st_t);
         macro_reduce_kernel<Q, St><<<(unsigned)chunks, RED_THREADS, 0, st>>>(
-            (const typename St::T *)d.pdf.p, view, odd, p, rho, u, u_stride, order, nullptr);
+            (const typename St::T *)d.cur_pdf(), view, odd, p, rho, u, u_stride, order, nullptr);
         return cudaGetLastError();
     });
 }
@@ -170,13 +193,13 @@ cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order,
 cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st) {
     const int64_t chunks = d.red_chunks();
     if (chunks == 0) return cudaMemsetAsync(out_dev, 0, 5 * sizeof(double), st);
-    const bool odd = d.step & 1;
+    const bool odd = d.pull() ? d.step > 0 : (d.step & 1);
     const CollideParams p = d.collide_params();
     cudaError_t e = with_types(d, [&](auto qtag, auto st_t, auto view) -> cudaError_t {
         constexpr int Q = decltype(qtag)::value;
         using St = decltype(st_t);
         macro_reduce_kernel<Q, St><<<(unsigned)chunks, RED_THREADS, 0, st>>>(
-            (const typename St::T *)d.pdf.p, view, odd, p, nullptr, nullptr, 0, 0, (double *)d.red_partial.p);
+            (const typename St::T *)d.cur_pdf(), view, odd, p, nullptr, nullptr, 0, 0, (double *)d.red_partial.p);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -186,7 +209,7 @@ cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st) {
 
 cudaError_t launch_init_equilibrium(const Domain &d, const float *rho, const float *u, int order,
                                     cudaStream_t st) {
-    const int64_t n = d.layout == SLBM_LAYOUT_SPARSE ? d.n_fluid : d.n_vox;
+    const int64_t n = d.sparse() ? d.n_fluid : d.n_vox;
     if (n == 0) return cudaSuccess;
     const int64_t u_stride = order == SLBM_ORDER_VOXELS ? d.n_vox : n;
     const float scale = d.collide_params().scale;

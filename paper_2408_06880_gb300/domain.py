@@ -190,6 +190,16 @@ class Domain:
         return dict(cell_voxel=cv[:nf], P=P[:, :S], link_cell=lc[:nl], link_dir=ld[:nl], link_type=lt[:nl],
                     n_fluid=nf, stride=S)
 
+    def export_codes(self) -> tuple[np.ndarray, np.ndarray]:
+        """The odd step's 16-bit link codes ((Q-1) x S uint16) and their
+        column bases ((S/128) x (Q-1) int32)."""
+        inf = self.info
+        S, q = inf["stride"], inf["q"]
+        codes = np.zeros((q - 1, max(S, 1)), np.uint16)
+        bases = np.zeros((max(S // 128, 1), q - 1), np.int32)
+        A.check(A.lib().sparse_lbm_export_codes(self.h, codes.ctypes.data, bases.ctypes.data))
+        return codes[:, :S], bases[:S // 128]
+
     def get_state(self):
         nb = C.c_int64()
         A.check(A.lib().sparse_lbm_state_bytes(self.h, C.byref(nb)))

@@ -157,7 +157,8 @@ def test_reductions_match_fields_and_are_deterministic():
 
 
 SHAPES = [(64, 1, 0), (128, 1, 0), (256, 1, 0), (64, 2, 0), (256, 2, 0), (128, 4, 0), (256, 4, 0),
-          (64, 2, 1), (64, 4, 1), (128, 2, 1), (128, 4, 1), (64, 1, 2), (128, 1, 2), (128, 1, 3), (64, 1, 3), (128, 2, 2)]
+          (64, 2, 1), (64, 4, 1), (128, 2, 1), (128, 4, 1), (64, 1, 2), (128, 1, 2), (128, 1, 3), (64, 1, 3), (128, 2, 2),
+          (128, 1, 4), (64, 1, 4), (128, 2, 4), (256, 2, 4)]
 
 
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
@@ -262,3 +263,64 @@ def test_invalid_calls_report_status():
             d.set_launch(1, 128, 4)
         with pytest.raises(P.SlbmError):
             d.step(-1)
+
+
+def _flip_rows(Pc, S, inv):
+    """The odd-step slot R from the canonical pull list: each non-negative
+    entry's row swapped between i and inverse(i)."""
+    R = Pc.astype(np.int64).copy()
+    for r in range(Pc.shape[0]):
+        i = r + 1
+        e = R[r]
+        m = e >= 0
+        row = e[m] // S
+        R[r, m] = np.where(row == i, inv[i], i) * S + (e[m] - row * S)
+    return R
+
+
+@pytest.mark.parametrize("case", ["periodic_64", "mixed_bc_q27", "walled_sparse"])
+def test_link_codes_decode_to_the_slot_list(case):
+    # the 16-bit codes plus bases reproduce every odd-step slot exactly
+    # (escapes read the int32 entry), and stepping through them (variant 4)
+    # gives the same bits as the int32 list
+    if case == "periodic_64":        # 131k cells: tiles at the z wrap span too wide
+        g, q = G.boolean_spheres(64, 0.5, 3), 19
+    elif case == "mixed_bc_q27":     # inlet/outlet links escape
+        g, q = _mixed_bc(13, (40, 33, 29)), 27
+    else:
+        g, q = G.random_solids((96, 80, 72), 0.9, 5, periodic=0), 19
+    _, _, inv = O.stencil(q)
+    kw = dict(q=q, op=P.TRT, force=(1e-5, 2e-6, 0.0))
+    with gpu_domain(g, **kw) as d:
+        lists = d.export_lists()
+        codes, bases = d.export_codes()
+        S, nf = lists["stride"], lists["n_fluid"]
+        R = _flip_rows(lists["P"], S, inv)
+        k = np.arange(S)
+        n_fluid_codes = n_escape = 0
+        for r in range(q - 1):
+            i = r + 1
+            c = codes[r].astype(np.int64)
+            b = bases[k // 128, r].astype(np.int64)
+            dec = np.where((b < 0) | (c == 0xFFFE), R[r], np.where(c == 0xFFFF, i * S + k, inv[i] * S + b + c))
+            assert np.array_equal(dec[:nf], R[r, :nf])
+            assert np.all((c[nf:] == 0xFFFF) | (b[nf:] < 0))
+            assert np.all(c[b < 0] == 0xFFFE)
+            # escapes in narrow tiles are exactly the inlet/outlet links
+            assert np.array_equal((c[:nf] == 0xFFFE) & (b[:nf] >= 0), (R[r, :nf] < 0) & (b[:nf] >= 0))
+            n_fluid_codes += int(np.count_nonzero((c[:nf] < 0xFFFE) & (b[:nf] >= 0)))
+            n_escape += int(np.count_nonzero(c[:nf] == 0xFFFE))
+        assert n_fluid_codes > 0
+        if case != "walled_sparse":
+            assert n_escape > 0
+        assert n_escape < 0.05 * nf * (q - 1)
+        d.set_launch(1, 128, 1, 0)
+        d.step(6)
+        want, _ = d.get_state()
+    with gpu_domain(g, **kw) as d:
+        m0 = d.memory_bytes()
+        d.set_launch(1, 128, 1, 4)              # builds the codes on first use
+        assert d.memory_bytes() > m0
+        d.step(6)
+        got, _ = d.get_state()
+    assert np.array_equal(got, want)
