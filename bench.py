@@ -251,6 +251,7 @@ def run_ours(a, rank, world):
            "roofline": roofline, "per_porosity": per, "clocks": clk, "gpu_launches": n_launch}
     if not a.no_extras and rank == 0:
         out["dense"] = bench_dense(a, P, stream, peak)
+        out["pull"] = bench_pull(a, P, stream, peak, per)
         out["fp16"] = bench_storage(a, P, stream, P.FP16, per)
         out["e2e"] = bench_e2e(a, P)
         if world == 1:
@@ -310,6 +311,33 @@ def bench_dense(a, P, stream, peak, pairs=10):
         ms = e0.elapsed_time(e1) / (2 * pairs)
         nf = d.n_fluid
         res.append({"porosity": phi, "mflups": round(nf / (ms / 1e3) / 1e6, 1),
+                    "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)})
+        d.close()
+    return res
+
+
+def bench_pull(a, P, stream, peak, per32, pairs=10):
+    """The two-grid pull scheme (Sec. 5.1's comparison) on the same geometries:
+    fluid MFLUPS, GB/s at its algorithmic bytes (2 Q B_pdf + (Q-1) 4 per
+    update), and the AA pattern's speed-up over it."""
+    import torch
+    res = []
+    for phi, aa in zip(a.porosities, per32):
+        g = geometry_for(phi, a.size)
+        d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+                     layout=P.SPARSE_PULL, stream=stream)
+        d.step(4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.step(2 * pairs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (2 * pairs)
+        nf = d.n_fluid
+        gbs = nf * (2 * Q * 4 + (Q - 1) * B_IDX) / (ms / 1e3) / 1e9
+        m = nf / (ms / 1e3) / 1e6
+        res.append({"porosity": phi, "mflups": round(m, 1), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                    "aa_speedup": round(aa["mflups"] / m, 4),
                     "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)})
         d.close()
     return res
