@@ -2,29 +2,31 @@
 #pragma once
 
 #include <mutex>
+#include <tuple>
 
 #include "aa_kernels.cuh"
 #include "internal.h"
 
 namespace slbm {
 
-// Persistent grid: SMs x resident CTAs of this kernel on the current device
-// (looked up once per kernel and device).
+// Persistent grid: SMs x resident CTAs of this kernel at this block size and
+// dynamic shared memory on the current device (looked up once each).
 template <class K>
-static unsigned persistent_grid(K kernel, int threads, int64_t tiles) {
+static unsigned persistent_grid(K kernel, int threads, int64_t tiles, size_t smem = 0) {
     static std::mutex mu;
-    static std::map<std::pair<int, const void *>, int> cache;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
     int slots;
     {
         std::lock_guard<std::mutex> lock(mu);
-        auto it = cache.find({dev, (const void *)kernel});
+        const auto key = std::make_tuple(dev, (const void *)kernel, threads, smem);
+        auto it = cache.find(key);
         if (it == cache.end()) {
             int sms = 1, ctas = 1;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kernel, threads, 0);
-            it = cache.emplace(std::make_pair(dev, (const void *)kernel), std::max(sms, 1) * std::max(ctas, 1)).first;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, kernel, threads, smem);
+            it = cache.emplace(key, std::max(sms, 1) * std::max(ctas, 1)).first;
         }
         slots = it->second;
     }
