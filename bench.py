@@ -196,14 +196,12 @@ def run_ours(a, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed_ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    # whole job: the updates of every rank over the slowest rank's time
+    from paper_2408_06880_gb300 import replicas
     updates_rank = sum(d.n_fluid for _, _, d in doms) * a.lbm_steps * a.steps
-    value = updates_rank * world / (elapsed_ms / 1e3) / 1e6
+    rate, _, secs = replicas.job_rate(updates_rank, elapsed_ms / 1e3)
+    elapsed_ms = secs * 1e3
+    value = rate / 1e6
 
     # per-kernel durations from the events recorded on the launching stream
     per = []
@@ -451,72 +449,98 @@ def serve_requests(n, max_steps):
 
 def run_serve(a):
     """Serve mode: continuous batching of the request stream (closed batch or
-    Poisson arrivals), optionally against one-at-a-time solves."""
+    Poisson arrivals), optionally against one-at-a-time solves.  Under
+    torchrun every rank serves its share of the requests on its own GPU
+    (replicas, no exchange); rank 0 reports the whole job."""
     import torch
     import paper_2408_06880_gb300 as P
-    from paper_2408_06880_gb300.serving import GpuExecutor, Server, solve_alone
+    from paper_2408_06880_gb300 import replicas
+    from paper_2408_06880_gb300.serving import GpuExecutor, serve_replicas, solve_alone
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    rank, world = replicas.rank_world()
     storage = {"fp32": P.FP32, "fp16": P.FP16, "bf16": P.BF16}[a.storage]
     reqs = serve_requests(a.requests, a.max_steps)
     out = {"metric": "solves/s (continuous batching, permeability requests)", "unit": "solves/s",
-           "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "storage": a.storage,
+           "n_gpus": world, "higher_is_better": True, "data": "synthetic", "storage": a.storage,
+           "scaling": "strong" if world > 1 else "weak",
            "config": {"workload": f"{a.requests} permeability requests: periodic Boolean packings, edge "
                                   f"{{64,96,128,192}}, porosity U(0.3,0.8), D3Q19 TRT F=1e-6, converge to "
                                   f"1e-6 relative change of mean u_x per 100 steps or {a.max_steps} steps",
                       "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals,
                       "pool_graph": bool(a.pool_graph), "group_mb": a.group_mb,
-                      "pool_streams": a.pool_streams}}
+                      "pool_streams": a.pool_streams,
+                      "parallelism": f"request replicas x{world}" if world > 1 else "single GPU"}}
     ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph),
                      group_bytes=None if a.group_mb is None else int(a.group_mb * 2 ** 20),
                      streams=a.pool_streams)
-    srv = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100)
+    budget = int(a.budget_gb * 2 ** 30)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
-    res, st = srv.run(reqs, realtime=False)
+    res, st = serve_replicas(ex, reqs, budget, realtime=False, chunk=100)
     out["clocks"] = clocks.stop()
     out["closed_batch"] = st
     out["value"] = round(st["solves_per_s"], 4)
     if a.arrivals == "poisson":
-        rate = a.load * st["solves_per_s"]
+        # arrivals over the whole stream at `load` x the measured capacity
+        rate = a.load * (st["solves_per_s"] if rank == 0 else 0.0)
+        rate = replicas.job_rate(rate, 1.0)[1]              # rank 0's value, on every rank
         rng = np.random.default_rng(4100)
         t = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
         for r, ti in zip(reqs, t):
             r.arrival = float(ti)
-        res_p, st_p = Server(ex, budget_bytes=int(a.budget_gb * 2 ** 30), chunk=100).run(reqs, realtime=True)
+        _, st_p = serve_replicas(ex, reqs, budget, realtime=True, chunk=100)
         out["poisson"] = dict(st_p, rate_per_s=rate)
     ex.close()
     out["results"] = [{"rid": r.rid, "k": r.permeability, "steps": r.steps, "converged": r.converged,
                        "latency_s": round(r.latency, 4), "error": r.error} for r in sorted(res, key=lambda r: r.rid)]
     if a.sequential:
+        mine = replicas.shard(reqs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        alone = [solve_alone(r, storage=storage) for r in reqs]
+        alone = [solve_alone(r, storage=storage) for r in mine]
         wall = time.perf_counter() - t0
-        lat = np.array([r.latency for r in alone])          # service time of each solve
-        seq = {"solves_per_s": len(alone) / wall, "wall_s": wall,
-               "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99))}
-        if a.arrivals == "poisson":
-            # a one-at-a-time FIFO server under the same arrivals, replayed
-            # from the measured service times
-            done, fifo = 0.0, []
-            for r, s in sorted(zip(reqs, lat), key=lambda x: (x[0].arrival, x[0].rid)):
-                done = max(done, r.arrival) + s
-                fifo.append(done - r.arrival)
-            seq["poisson_fifo"] = {"latency_p50_s": float(np.percentile(fifo, 50)),
-                                   "latency_p99_s": float(np.percentile(fifo, 99)),
-                                   "latency_mean_s": float(np.mean(fifo))}
-        out["one_at_a_time"] = seq
-        k_alone = {r.rid: r.permeability for r in alone}
-        out["served_equals_alone"] = all(r.permeability == k_alone[r.rid] for r in res if r.error is None)
-        steps_alone = {r.rid: r.steps for r in alone}
-        out["served_steps_equal_alone"] = all(r.steps == steps_alone[r.rid] for r in res if r.error is None)
+        sps, _, wall_max = replicas.job_rate(len(alone), wall)
+        # service times and one-at-a-time FIFO latencies per rank (each rank
+        # a FIFO server of its share under the same arrivals)
+        done, fifo = 0.0, []
+        lat = [r.latency for r in alone]
+        for r, s_ in sorted(zip(mine, lat), key=lambda x: (x[0].arrival, x[0].rid)):
+            done = max(done, r.arrival) + s_
+            fifo.append(done - r.arrival)
+        parts = replicas.gather((alone, lat, fifo))
+        if parts is not None:
+            alone = [r for p_ in parts for r in p_[0]]
+            lat = np.array([x for p_ in parts for x in p_[1]])
+            fifo = np.array([x for p_ in parts for x in p_[2]])
+            seq = {"solves_per_s": sps, "wall_s": wall_max,
+                   "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99))}
+            if a.arrivals == "poisson":
+                seq["poisson_fifo"] = {"latency_p50_s": float(np.percentile(fifo, 50)),
+                                       "latency_p99_s": float(np.percentile(fifo, 99)),
+                                       "latency_mean_s": float(np.mean(fifo))}
+            out["one_at_a_time"] = seq
+            k_alone = {r.rid: r.permeability for r in alone}
+            out["served_equals_alone"] = all(r.permeability == k_alone[r.rid] for r in res if r.error is None)
+            steps_alone = {r.rid: r.steps for r in alone}
+            out["served_steps_equal_alone"] = all(r.steps == steps_alone[r.rid] for r in res if r.error is None)
     return out
 
 
 def main():
     a = parse()
     if a.mode == "serve" and a.impl == "ours":
-        print(json.dumps(run_serve(a)), flush=True)
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+        out = run_serve(a)
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -271,6 +271,29 @@ class Server:
                 "converged": sum(r.converged for r in ok)}
 
 
+def serve_replicas(executor, requests: list[Request], budget_bytes: int, realtime: bool = False,
+                   chunk: int = 100, **server_kw) -> tuple[list[Result], dict]:
+    """Serve a request stream over all ranks of the process group (one GPU
+    each, no exchange on the data path): request i goes to rank i mod world,
+    each rank serves its share with its own executor, and rank 0 gets every
+    result plus the whole-job statistics -- solves over the slowest rank's
+    wall time, latency percentiles over all requests.  Other ranks get their
+    own results and local statistics.  Collective: every rank must call it."""
+    from . import replicas
+    mine = replicas.shard(requests)
+    res, st = Server(executor, budget_bytes, chunk=chunk, **server_kw).run(mine, realtime=realtime)
+    upd_local = st["mflups"] * 1e6 * st["wall_s"] if st["wall_s"] > 0 else 0.0
+    _, updates, wall = replicas.job_rate(upd_local, st["wall_s"])
+    _, busy_sum, _ = replicas.job_rate(st["device_busy_s"], st["wall_s"])
+    parts = replicas.gather(res)
+    if parts is None:
+        return res, st
+    allres = [r for part in parts for r in part]
+    merged = Server.stats(allres, wall, busy_sum, int(round(updates)))
+    merged["ranks"] = len(parts)
+    return allres, merged
+
+
 def solve_alone(req: Request, q: int = 19, storage: int = A.FP32, chunk: int = 100, graph: bool = True,
                 scale_exp: int | None = None, stream=None) -> Result:
     """One request on its own (no pool): the one-at-a-time baseline, with the
