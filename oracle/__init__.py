@@ -9,8 +9,10 @@ seeded input generator package ``geometry`` (no LBM arithmetic there).
 Contents (each function cites the passage it follows):
 
 * ``oracle.c`` (plain C, FP64, compiled here with gcc): stencils, Eq. 1
-  moments, Eq. 6 equilibrium, Eq. 5 SRT / textbook TRT collision with a Guo
-  force, a dense direct-addressing two-grid PUSH stepper (Sec. 2-3), the
+  moments, Eq. 6 equilibrium, Eq. 5 SRT / textbook TRT / D3Q19 MRT (the
+  orthogonal moment basis of d'Humieres et al. 2002; Sec. 4 lists MRT among
+  the operators) collision with a Guo force, a dense direct-addressing
+  two-grid PUSH stepper (Sec. 2-3), the
   compacted cell order and the pull index-list (Sec. 3.1, 3.1.1) and a sparse
   two-grid PULL stepper on that list.
 * this module: ctypes marshalling, the TRT rate from the magic parameter, the
@@ -20,7 +22,7 @@ Contents (each function cites the passage it follows):
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, invariants, brute force on tiny inputs, the paper's printed
 table values); the inlet/outlet boundary maps are pinned only by Couette
-(closed form) and a plug-flow flux invariant, see the design doc.
+(closed form) and a plug-flow flux invariant.
 """
 from __future__ import annotations
 
@@ -39,7 +41,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-SRT, TRT = 0, 1
+SRT, TRT, MRT = 0, 1, 2
 FLUID, WALL, INLET, OUTLET = 0, 1, 2, 3
 PAD = np.iinfo(np.int32).min
 
@@ -60,7 +62,8 @@ class _Problem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("flags", C.c_void_p), ("periodic", C.c_uint32), ("q", C.c_int32),
                 ("op", C.c_int32), ("omega_plus", C.c_double), ("omega_minus", C.c_double),
-                ("force", C.c_double * 3), ("inlet_u", C.c_void_p), ("rho_out", C.c_double)]
+                ("force", C.c_double * 3), ("inlet_u", C.c_void_p), ("rho_out", C.c_double),
+                ("mrt_s", C.c_double * 19)]
 
 
 def lib():
@@ -75,6 +78,7 @@ def lib():
             L.orc_guo_source.argtypes = [C.c_int, vp, vp, vp]
             L.orc_moments.argtypes = [C.c_int, vp, vp, vp, vp]
             L.orc_collide.argtypes = [P, vp, vp]
+            L.orc_mrt_matrix.argtypes = [vp]
             L.orc_dense_init.argtypes = [P, vp, vp, vp]
             L.orc_dense_run.argtypes = [P, vp, C.c_int]
             L.orc_dense_macroscopic.argtypes = [P, vp, vp, vp]
@@ -102,6 +106,23 @@ def trt_omega_minus(omega_plus: float, magic: float) -> float:
     return 1.0 / (magic / (1.0 / omega_plus - 0.5) + 0.5)
 
 
+def mrt_default_rates(omega: float) -> tuple:
+    """Per-moment MRT rates of d'Humieres et al. (2002) for the D3Q19 basis
+    order (rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy,
+    pyz, pxz, mx, my, mz): conserved moments 0, s_e = 1.19, s_eps = s_pi =
+    1.4, s_q = 1.2, s_m = 1.98, and omega (Eq. 7) on the stress moments."""
+    w = float(omega)
+    return (0.0, 1.19, 1.4, 0.0, 1.2, 0.0, 1.2, 0.0, 1.2, w, 1.4, w, 1.4, w, w, w, 1.98, 1.98, 1.98)
+
+
+def mrt_matrix() -> np.ndarray:
+    """The oracle's D3Q19 MRT moment matrix M[a, i] (rows: the basis of
+    d'Humieres et al. 2002, columns: the velocity table)."""
+    M = np.zeros((19, 19))
+    lib().orc_mrt_matrix(_ptr(M))
+    return M
+
+
 @dataclass
 class Problem:
     """A voxel geometry plus the method's parameters (Sec. 2: stencil,
@@ -116,6 +137,7 @@ class Problem:
     force: tuple = (0.0, 0.0, 0.0)
     inlet_u: np.ndarray | None = None
     rho_out: float = 1.0
+    mrt_rates: tuple | None = None    # MRT: 19 per-moment rates (default mrt_default_rates)
 
     @classmethod
     def from_geometry(cls, g, **kw):
@@ -146,9 +168,12 @@ class Problem:
         self._inlet_c = (None if self.inlet_u is None
                          else np.ascontiguousarray(self.inlet_u, dtype=np.float64).reshape(-1))
         nx, ny, nz = self.shape
+        if self.op == MRT and self.q != 19:
+            raise ValueError("the MRT operator is defined for D3Q19")
+        rates = self.mrt_rates if self.mrt_rates is not None else mrt_default_rates(self.omega_plus)
         s = _Problem(nx, ny, nz, _ptr(self._flags_c), self.periodic, self.q, self.op,
                      self.omega_plus, self.omega_minus, (C.c_double * 3)(*self.force),
-                     _ptr(self._inlet_c), self.rho_out)
+                     _ptr(self._inlet_c), self.rho_out, (C.c_double * 19)(*rates))
         self._cs = s
         return C.byref(s)
 

@@ -11,6 +11,9 @@
  *     with SRT  Omega_i = -omega (f_i - f_i^eq)                           (Eq. 5)
  *     or TRT (two relaxation rates on the even/odd parts; textbook form,
  *     the paper names TRT in Sec. 4 and cites the LBM textbook for it),
+ *     or MRT (D3Q19: relaxation in the orthogonal moment space of
+ *     d'Humieres et al. 2002, one rate per moment; the paper lists MRT among
+ *     its generated operators, Sec. 4, and benchmarks it in Sec. 5.1),
  *     second-order equilibrium f_i^eq                                     (Eq. 6)
  *     and a Guo body-force source (the paper says only "a force model",
  *     Sec. 4; the Guo form is our reading)
@@ -37,7 +40,7 @@
 #endif
 
 enum { ORC_FLUID = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3 };
-enum { ORC_SRT = 0, ORC_TRT = 1 };
+enum { ORC_SRT = 0, ORC_TRT = 1, ORC_MRT = 2 };
 
 /* Velocity set, directions written out one by one (D3Q19 is the first 19
  * rows of D3Q27).  Ordering convention: rest, then the six axis directions,
@@ -62,6 +65,7 @@ typedef struct {
     double force[3];           /* body-force density (Guo) */
     const double *inlet_u;     /* 3 per inlet voxel, ascending voxel order; may be NULL */
     double rho_out;            /* outlet density */
+    double mrt_s[19];          /* ORC_MRT (D3Q19): relaxation rate of each moment of the basis below */
 } orc_problem;
 
 /* ---------------------------------------------------------------- stencil */
@@ -132,13 +136,84 @@ void orc_moments(int q, const double *f, const double F[3], double *rho_out, dou
     for (int a = 0; a < 3; ++a) u_out[a] = (j[a] + 0.5 * F[a]) / rho;
 }
 
-/* One cell's collision (Eq. 3 with Eq. 5 or TRT): f -> fs. */
+/* D3Q19 moment basis of d'Humieres, Ginzburg, Krafczyk, Lallemand, Luo
+ * (2002), row a evaluated at velocity c = (x, y, z), |c|^2 = n:
+ *   0 rho 1              1 e  19n - 30          2 eps (21n^2 - 53n + 24)/2
+ *   3 jx  x              4 qx (5n - 9) x        5 jy  y     6 qy (5n - 9) y
+ *   7 jz  z              8 qz (5n - 9) z
+ *   9 3pxx 3x^2 - n      10 3pixx (3n - 5)(3x^2 - n)
+ *   11 pww y^2 - z^2     12 piww (3n - 5)(y^2 - z^2)
+ *   13 pxy xy   14 pyz yz   15 pxz xz
+ *   16 mx x(y^2 - z^2)   17 my y(z^2 - x^2)   18 mz z(x^2 - y^2)
+ * The rows are mutually orthogonal over the 19 velocities (a test checks
+ * it), so M^-1 = M^T diag(1 / |row a|^2). */
+static double mrt_row(int a, int i) {
+    double x = VEL[i][0], y = VEL[i][1], z = VEL[i][2], n = x * x + y * y + z * z;
+    switch (a) {
+        case 0: return 1.0;
+        case 1: return 19.0 * n - 30.0;
+        case 2: return (21.0 * n * n - 53.0 * n + 24.0) / 2.0;
+        case 3: return x;
+        case 4: return (5.0 * n - 9.0) * x;
+        case 5: return y;
+        case 6: return (5.0 * n - 9.0) * y;
+        case 7: return z;
+        case 8: return (5.0 * n - 9.0) * z;
+        case 9: return 3.0 * x * x - n;
+        case 10: return (3.0 * n - 5.0) * (3.0 * x * x - n);
+        case 11: return y * y - z * z;
+        case 12: return (3.0 * n - 5.0) * (y * y - z * z);
+        case 13: return x * y;
+        case 14: return y * z;
+        case 15: return x * z;
+        case 16: return x * (y * y - z * z);
+        case 17: return y * (z * z - x * x);
+        default: return z * (x * x - y * y);
+    }
+}
+
+/* The 19 x 19 matrix M[a][i] (row-major), for the tests. */
+void orc_mrt_matrix(double *M) {
+    for (int a = 0; a < 19; ++a)
+        for (int i = 0; i < 19; ++i) M[a * 19 + i] = mrt_row(a, i);
+}
+
+/* MRT collision in moment space (D3Q19):
+ *   m = M f, m_eq = M f_eq, m_F = M S (Guo source)
+ *   m*_a = m_a - s_a (m_a - m_eq_a) + (1 - s_a/2) m_F_a
+ *   f* = M^-1 m* */
+static void collide_mrt(const orc_problem *p, const double *f, const double *feq, const double *S, double *fs) {
+    double m[19], me[19], mf[19], nrm[19];
+    for (int a = 0; a < 19; ++a) {
+        m[a] = me[a] = mf[a] = nrm[a] = 0.0;
+        for (int i = 0; i < 19; ++i) {
+            double r = mrt_row(a, i);
+            m[a] += r * f[i];
+            me[a] += r * feq[i];
+            mf[a] += r * S[i];
+            nrm[a] += r * r;
+        }
+        double s = p->mrt_s[a];
+        m[a] = m[a] - s * (m[a] - me[a]) + (1.0 - 0.5 * s) * mf[a];
+    }
+    for (int i = 0; i < 19; ++i) {
+        double v = 0.0;
+        for (int a = 0; a < 19; ++a) v += mrt_row(a, i) * m[a] / nrm[a];
+        fs[i] = v;
+    }
+}
+
+/* One cell's collision (Eq. 3 with Eq. 5, TRT or MRT): f -> fs. */
 void orc_collide(const orc_problem *p, const double *f, double *fs) {
     int q = p->q;
     double rho, u[3], feq[27], S[27];
     orc_moments(q, f, p->force, &rho, u);
     orc_equilibrium(q, rho, u, feq);
     orc_guo_source(q, u, p->force, S);
+    if (p->op == ORC_MRT) {
+        collide_mrt(p, f, feq, S, fs);
+        return;
+    }
     double wp = p->omega_plus;
     if (p->op == ORC_SRT) {
         for (int i = 0; i < q; ++i)
