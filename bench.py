@@ -250,6 +250,7 @@ def run_ours(a, rank, world):
     if not a.no_extras and rank == 0:
         out["dense"] = bench_dense(a, P, stream, peak)
         out["pull"] = bench_pull(a, P, stream, peak, per)
+        out["operators"] = bench_operators(a, P, stream, peak)
         out["fp16"] = bench_storage(a, P, stream, P.FP16, per)
         out["e2e"] = bench_e2e(a, P)
         if world == 1:
@@ -339,6 +340,36 @@ def bench_pull(a, P, stream, peak, per32, pairs=10):
                     "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)})
         d.close()
     return res
+
+
+def bench_operators(a, P, stream, peak, pairs=10):
+    """Sec. 5.1's comparison of streaming patterns per collision operator:
+    AA and pull MFLUPS for SRT, TRT and MRT on the porosity-0.5 domain
+    (GB/s at each scheme's algorithmic bytes)."""
+    import torch
+    phi = 0.5 if 0.5 in a.porosities else a.porosities[0]
+    g = geometry_for(phi, a.size)
+    res = []
+    for name, op in (("SRT", P.SRT), ("TRT", P.TRT), ("MRT", P.MRT)):
+        row = {"op": name}
+        for scheme, layout, idx in (("aa", P.SPARSE, (Q - 1) * B_IDX / 2), ("pull", P.SPARSE_PULL, (Q - 1) * B_IDX)):
+            d = P.Domain(g.flags, periodic=7, q=Q, op=op, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+                         layout=layout, stream=stream)
+            d.step(4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d.step(2 * pairs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (2 * pairs)
+            nf = d.n_fluid
+            m = nf / (ms / 1e3) / 1e6
+            gbs = nf * (2 * Q * 4 + idx) / (ms / 1e3) / 1e9
+            row[scheme] = {"mflups": round(m, 1), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+            d.close()
+        row["aa_over_pull"] = round(row["aa"]["mflups"] / row["pull"]["mflups"], 4)
+        res.append(row)
+    return {"porosity": phi, "rows": res}
 
 
 def bench_storage(a, P, stream, storage, per32, pairs=20):

@@ -59,7 +59,7 @@ typedef enum {
     SLBM_EDEVICE = 8        /* a device-side check latched an error (checked kernels) */
 } slbm_status;
 
-enum { SLBM_SRT = 0, SLBM_TRT = 1 };
+enum { SLBM_SRT = 0, SLBM_TRT = 1, SLBM_MRT = 2 };
 enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
 enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1, SLBM_LAYOUT_SPARSE_PULL = 2 };
 enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
@@ -71,7 +71,7 @@ typedef struct {
     const uint8_t *flags;      /* HOST, nx*ny*nz flags (0..3), read during create only */
     uint32_t periodic;         /* bit0 x, bit1 y, bit2 z */
     int32_t q;                 /* 19 or 27 */
-    int32_t op;                /* SLBM_SRT or SLBM_TRT */
+    int32_t op;                /* SLBM_SRT, SLBM_TRT or SLBM_MRT (D3Q19, sparse and pull layouts) */
     double omega_plus;         /* 1/tau in (0, 2) (Eq. 7) */
     double trt_magic;          /* TRT magic parameter Lambda > 0; ignored for SRT */
     double force[3];           /* constant body-force density (Guo) */
@@ -85,6 +85,17 @@ typedef struct {
                                   (comparison scheme: the same lists, two fields, pull) */
     int32_t reserved;          /* must be 0 */
 } slbm_desc;
+
+/* SLBM_MRT -- multiple-relaxation-time collision (D3Q19 only; the paper
+ * lists MRT among its generated operators, Sec. 4, and benchmarks it against
+ * SRT/TRT in Sec. 5.1).  Relaxation happens in the orthogonal moment basis of
+ * d'Humieres et al. (2002), rows in the order rho, e, eps, jx, qx, jy, qy,
+ * jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx, my, mz, with the Guo
+ * force: m* = m - S (m - m_eq) + (I - S/2) M F.  Rates: omega_plus on the
+ * five stress moments (the viscosity, Eq. 7) and, until
+ * sparse_lbm_set_mrt_rates says otherwise, s_e = 1.19, s_eps = s_pi = 1.4,
+ * s_q = 1.2, s_m = 1.98; trt_magic is ignored.  Sparse (AA) and pull
+ * layouts, launch variants 0 and 2; no pools. */
 
 /* SLBM_LAYOUT_SPARSE_PULL -- the two-grid pull scheme the paper compares the
  * AA pattern with (Sec. 5.1, Table 2's pull row): the same compacted cells and
@@ -196,6 +207,12 @@ slbm_status sparse_lbm_export_codes(slbm_t *h, uint16_t *codes, int32_t *bases);
 slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes);
 slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step);
 slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
+
+/* MRT domains: the relaxation rate of every moment of the basis (19 values
+ * in the basis order; the conserved rho, jx, jy, jz entries are ignored; the
+ * others must lie in (0, 2)).  The stress entries (9, 11, 13, 14, 15) set
+ * the viscosity.  SLBM_EINVAL for non-MRT domains or rates out of range. */
+slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
 
 /* Launch shape used for a parity (0 even, 1 odd), chosen by the autotuner.
  * variant 0: `cells` cells per thread (even 1/2/4 consecutive cells; odd 1/2

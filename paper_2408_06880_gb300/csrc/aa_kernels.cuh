@@ -119,7 +119,7 @@ __device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
     }
 }
 
-template <int Q, int ST, int CPT>
+template <int Q, int ST, int CPT, int OP = OP_TRT>
 __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
                                                       int32_t nf, CollideParams p) {
     using St = Store<ST>;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
         for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
     }
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+    for (int c = 0; c < CPT; ++c) collide_op<Q, St::scaled, OP>(g[c], p);
     const bool full = k0 + CPT <= nf;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -170,7 +170,8 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // CODE: the slots come from the 16-bit link codes and their per-tile column
 // bases (2 bytes per link instead of 4); an escape code reads the slot from
 // the int32 list.  The decoded slot equals R(i, k) exactly.
-template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false>
+template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false,
+          int OP = OP_TRT>
 __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                      const int32_t *__restrict__ P, int32_t S, int32_t nf,
                                                      const LinkMap *__restrict__ maps, int32_t n_links,
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
     }
     Vel u[CPT];
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) u[c] = collide<Q, St::scaled>(g[c], p);
+    for (int c = 0; c < CPT; ++c) u[c] = collide_op<Q, St::scaled, OP>(g[c], p);
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         const int32_t k = kb + c * blockDim.x;

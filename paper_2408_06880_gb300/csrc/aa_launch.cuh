@@ -97,12 +97,52 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
     return e;
 }
 
+// MRT domains (D3Q19): the plain even kernel (1 or 2 cells per thread) and
+// the odd kernel (1 or 2 cells, L2 index prefetch unless variant 0; checked
+// mode), with the MRT collision.
+template <int ST>
+static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    T *pdf = reinterpret_cast<T *>(d.pdf.p);
+    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
+    const LaunchShape sh = d.shape[parity];
+    const CollideParams p = d.collide_params();
+    auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
+    if (parity == 0) {
+        if (sh.cells == 1) aa_even_kernel<19, ST, 1, OP_MRT><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p);
+        else aa_even_kernel<19, ST, 2, OP_MRT><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+        return cudaGetLastError();
+    }
+    const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
+    const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
+    const int32_t nl = (int32_t)d.n_links;
+    int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
+    const bool bc = nl > 0;
+    if (d.checked) {
+        auto kc = bc ? aa_odd_kernel<19, ST, 1, true, true, false, false, OP_MRT>
+                     : aa_odd_kernel<19, ST, 1, false, true, false, false, OP_MRT>;
+        kc<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0, nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    const int cells = sh.cells == 2 ? 2 : 1;
+    auto k = cells == 1 ? (bc ? aa_odd_kernel<19, ST, 1, true, false, false, false, OP_MRT>
+                              : aa_odd_kernel<19, ST, 1, false, false, false, false, OP_MRT>)
+                        : (bc ? aa_odd_kernel<19, ST, 2, true, false, false, false, OP_MRT>
+                              : aa_odd_kernel<19, ST, 2, false, false, false, false, OP_MRT>);
+    const int32_t pf = sh.variant == 2 ? (int32_t)persistent_grid(k, sh.threads, INT32_MAX) : 0;
+    k<<<grid(cells), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
 template <int Q, int ST>
 static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
+    if constexpr (Q == 19) {
+        if (d.op == SLBM_MRT) return launch_mrt<ST>(d, parity, st);
+    }
     const LaunchShape sh = d.shape[parity];
     if (sh.variant >= 2 && parity == 0) return cudaErrorInvalidValue;
     if (sh.variant == 1 && !d.checked && ST != ST_BF16) {

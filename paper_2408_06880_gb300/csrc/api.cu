@@ -70,7 +70,7 @@ void Ctx::fail(slbm_status s, const char *msg) {
 }
 
 CollideParams Domain::collide_params() const {
-    CollideParams p;
+    CollideParams p{};
     p.omega_p = (float)omega_p;
     p.omega_m = (float)omega_m;
     p.fx = (float)force[0];
@@ -91,7 +91,15 @@ CollideParams Domain::collide_params() const {
         p.alpha[m] = (float)(sigma * kp * 9.0 * w * cF);
         p.kappa[m] = (float)(sigma * km * 3.0 * w * cF);
     }
+    for (int a = 0; a < 19; ++a) p.mrt[a] = (float)mrt_rates[a];
     return p;
+}
+
+// d'Humieres et al. (2002) rates with omega on the stress moments.
+static void default_mrt_rates(Domain &d) {
+    const double w = d.omega_p;
+    const double r[19] = {0, 1.19, 1.4, 0, 1.2, 0, 1.2, 0, 1.2, w, 1.4, w, 1.4, w, w, w, 1.98, 1.98, 1.98};
+    for (int a = 0; a < 19; ++a) d.mrt_rates[a] = r[a];
 }
 
 template <int Q>
@@ -205,7 +213,9 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (N >= ((int64_t)1 << 31)) return err(SLBM_EUNSUPPORTED, "nx*ny*nz must be < 2^31");
     if (!s.flags) return err(SLBM_EINVAL, "flags must be non-NULL");
     if (s.q != 19 && s.q != 27) return err(SLBM_EINVAL, "q must be 19 or 27");
-    if (s.op != SLBM_SRT && s.op != SLBM_TRT) return err(SLBM_EINVAL, "op must be SRT (0) or TRT (1)");
+    if (s.op != SLBM_SRT && s.op != SLBM_TRT && s.op != SLBM_MRT) return err(SLBM_EINVAL, "op must be SRT, TRT or MRT");
+    if (s.op == SLBM_MRT && (s.q != 19 || s.layout == SLBM_LAYOUT_DENSE))
+        return err(SLBM_EUNSUPPORTED, "MRT is built for D3Q19 sparse and pull layouts");
     if (!(s.omega_plus > 0.0 && s.omega_plus < 2.0)) return err(SLBM_EINVAL, "omega_plus must lie in (0, 2)");
     if (s.op == SLBM_TRT && !(s.trt_magic > 0.0 && std::isfinite(s.trt_magic)))
         return err(SLBM_EINVAL, "trt_magic must be > 0");
@@ -255,9 +265,10 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     d.omega_p = s.omega_plus;
     d.magic = s.trt_magic;
     d.omega_m = s.op == SLBM_TRT ? 1.0 / (s.trt_magic / (1.0 / s.omega_plus - 0.5) + 0.5) : s.omega_plus;
+    if (d.op == SLBM_MRT) default_mrt_rates(d);
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
-    if (d.storage == SLBM_FP16 && d.layout == SLBM_LAYOUT_SPARSE) d.shape[0] = LaunchShape{128, 2, 1};
+    if (d.storage == SLBM_FP16 && d.layout == SLBM_LAYOUT_SPARSE && d.op != SLBM_MRT) d.shape[0] = LaunchShape{128, 2, 1};
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -532,9 +543,26 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step) {
     return ok();
 }
 
+slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates) {
+    if (!h || !rates) return err(SLBM_EINVAL, "null argument");
+    Domain &d = h->d;
+    if (d.op != SLBM_MRT) return err(SLBM_EINVAL, "not an MRT domain");
+    for (int a = 0; a < 19; ++a) {
+        if (a == 0 || a == 3 || a == 5 || a == 7) continue;
+        if (!(rates[a] > 0.0 && rates[a] < 2.0)) return err(SLBM_EINVAL, "MRT rates must lie in (0, 2)");
+    }
+    for (int a = 0; a < 19; ++a) d.mrt_rates[a] = (a == 0 || a == 3 || a == 5 || a == 7) ? 0.0 : rates[a];
+    drop_graphs(d);
+    return ok();
+}
+
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
     if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
+    if (h->d.op == SLBM_MRT && variant != 0 && variant != 2)
+        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
+    if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
+        return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
     if (variant == 0) {
         if (threads < 32 || threads > 256 || threads % 32)
             return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");

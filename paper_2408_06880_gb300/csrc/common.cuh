@@ -98,6 +98,10 @@ struct CollideParams {
     //   kappa_m = sigma (1 - omega-/2) 3 w_i (c_i . F)
     float alpha[MAX_PAIRS];
     float kappa[MAX_PAIRS];
+    // MRT (D3Q19): relaxation rate of each moment of the basis below
+    // (conserved moments unused)
+    float mrt[19];
+    float pad;          // keeps the size a multiple of 8 bytes (zero)
 };
 
 // Boundary link of cell k, direction i (the pull neighbour x_k - c_i is an
@@ -226,6 +230,187 @@ __device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
         g[i + 1] = A - B;
     }
     return Vel{ux, uy, uz};
+}
+
+// ---------------------------------------------------------------- MRT
+// D3Q19 moment basis of d'Humieres, Ginzburg, Krafczyk, Lallemand, Luo
+// (2002), row a at velocity c = (x, y, z), |c|^2 = n:
+//   0 rho 1            1 e 19n - 30         2 eps (21n^2 - 53n + 24)/2
+//   3 jx x   4 qx (5n - 9)x   5 jy y   6 qy (5n - 9)y   7 jz z   8 qz (5n - 9)z
+//   9 3pxx 3x^2 - n    10 3pixx (3n - 5)(3x^2 - n)
+//   11 pww y^2 - z^2   12 piww (3n - 5)(y^2 - z^2)
+//   13 pxy xy  14 pyz yz  15 pxz xz
+//   16 mx x(y^2 - z^2)  17 my y(z^2 - x^2)  18 mz z(x^2 - y^2)
+// All entries are integers; the rows are orthogonal, so M^-1 = M^T / |row|^2.
+__host__ __device__ constexpr int mrt_m(int a, int i) {
+    const int x = cx(i), y = cy(i), z = cz(i), n = x * x + y * y + z * z;
+    switch (a) {
+        case 0: return 1;
+        case 1: return 19 * n - 30;
+        case 2: return (21 * n * n - 53 * n + 24) / 2;
+        case 3: return x;
+        case 4: return (5 * n - 9) * x;
+        case 5: return y;
+        case 6: return (5 * n - 9) * y;
+        case 7: return z;
+        case 8: return (5 * n - 9) * z;
+        case 9: return 3 * x * x - n;
+        case 10: return (3 * n - 5) * (3 * x * x - n);
+        case 11: return y * y - z * z;
+        case 12: return (3 * n - 5) * (y * y - z * z);
+        case 13: return x * y;
+        case 14: return y * z;
+        case 15: return x * z;
+        case 16: return x * (y * y - z * z);
+        case 17: return y * (z * z - x * x);
+        default: return z * (x * x - y * y);
+    }
+}
+
+__host__ __device__ constexpr int mrt_norm(int a) {
+    int s = 0;
+    for (int i = 0; i < 19; ++i) s += mrt_m(a, i) * mrt_m(a, i);
+    return s;
+}
+
+__host__ __device__ constexpr bool mrt_odd_row(int a) {
+    return (a >= 3 && a <= 8) || a >= 16;     // j, q, m: odd in c
+}
+
+// MRT collision in stored (shifted, scaled) units: with the non-equilibrium
+// part x_i = g_i - sigma (f_i^eq - w_i) and the Guo source sigma S_i,
+//   dm_a = -s_a (M x)_a + (1 - s_a/2) (M sigma S)_a   (non-conserved a)
+//   g*_i = g_i + sum_a M_ai dm_a / |row a|^2 + sigma (c_i . F) / 10
+// (the last term is the momentum rows' kick, |row jx|^2 = 10; the density
+// row changes nothing).  Every row is even or odd under c -> -c, so both
+// transforms run on the sums and differences of the 9 inverse pairs: an even
+// row sees g_0 and the pair sums, an odd row the pair differences, and the
+// back transform yields both members of a pair from one even and one odd sum.
+template <bool SCALED>
+__device__ __forceinline__ Vel collide_mrt(float (&g)[19], const CollideParams &p) {
+    constexpr int NP = 9;
+    float sg[NP], dg[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        sg[m] = g[2 * m + 1] + g[2 * m + 2];
+        dg[m] = g[2 * m + 1] - g[2 * m + 2];
+    }
+    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        drho += sg[m];
+        const int i = 2 * m + 1;
+        if (cx(i) > 0) jx += dg[m];
+        if (cx(i) < 0) jx -= dg[m];
+        if (cy(i) > 0) jy += dg[m];
+        if (cy(i) < 0) jy -= dg[m];
+        if (cz(i) > 0) jz += dg[m];
+        if (cz(i) < 0) jz -= dg[m];
+    }
+    if (SCALED) {
+        drho *= p.inv_scale;
+        jx *= p.inv_scale;
+        jy *= p.inv_scale;
+        jz *= p.inv_scale;
+    }
+    const float rho = 1.0f + drho;
+    const float ir = 1.0f / rho;
+    const float ux = fmaf(0.5f, p.fx, jx) * ir;
+    const float uy = fmaf(0.5f, p.fy, jy) * ir;
+    const float uz = fmaf(0.5f, p.fz, jz) * ir;
+    const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+    const float uF = fmaf(uz, p.fz, fmaf(uy, p.fy, ux * p.fx));
+    const float sig = SCALED ? p.scale : 1.0f;
+    // non-equilibrium and source, as pair sums (even) and differences (odd):
+    //   geq_i +- geq_ib = 2 w (drho + rho (4.5 cu^2 - 1.5 u.u)),  2 w 3 rho cu
+    //   S_i +- S_ib     = 2 w (9 cu cF - 3 u.F),                   2 w 3 cF
+    const float e0 = fmaf(-1.5f * rho, usq, drho);               // drho - 1.5 rho u.u
+    const float x0 = fmaf(-sig * wgt<19>(0), e0, g[0]);
+    const float s0 = -3.0f * sig * wgt<19>(0) * uF;
+    float xs[NP], xd[NP], ss[NP], sd[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int i = 2 * m + 1;
+        const float w2 = 2.0f * wgt<19>(i) * sig;
+        float cu = 0.f, cF = 0.f;
+        if (cx(i) > 0) { cu += ux; cF += p.fx; }
+        if (cx(i) < 0) { cu -= ux; cF -= p.fx; }
+        if (cy(i) > 0) { cu += uy; cF += p.fy; }
+        if (cy(i) < 0) { cu -= uy; cF -= p.fy; }
+        if (cz(i) > 0) { cu += uz; cF += p.fz; }
+        if (cz(i) < 0) { cu -= uz; cF -= p.fz; }
+        xs[m] = fmaf(-w2, fmaf(4.5f * rho * cu, cu, e0), sg[m]);
+        xd[m] = fmaf(-w2, 3.0f * rho * cu, dg[m]);
+        ss[m] = w2 * fmaf(9.0f * cu, cF, -3.0f * uF);
+        sd[m] = w2 * 3.0f * cF;
+    }
+    float dm[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        dm[a] = 0.f;
+        if (a == 0 || a == 3 || a == 5 || a == 7) continue;       // conserved
+        float mx = 0.f, ms = 0.f;
+        if (!mrt_odd_row(a)) {
+            mx = (float)mrt_m(a, 0) * x0;
+            ms = (float)mrt_m(a, 0) * s0;
+        }
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const int i = 2 * m + 1;
+            if (mrt_m(a, i) == 0) continue;
+            if (mrt_odd_row(a)) {
+                mx = fmaf((float)mrt_m(a, i), xd[m], mx);
+                ms = fmaf((float)mrt_m(a, i), sd[m], ms);
+            } else {
+                mx = fmaf((float)mrt_m(a, i), xs[m], mx);
+                ms = fmaf((float)mrt_m(a, i), ss[m], ms);
+            }
+        }
+        const float sa = p.mrt[a];
+        dm[a] = fmaf(-sa, mx, (1.0f - 0.5f * sa) * ms) * (1.0f / (float)mrt_norm(a));
+    }
+    {
+        float v = g[0];
+#pragma unroll
+        for (int a = 0; a < 19; ++a)
+            if (!mrt_odd_row(a) && a != 0 && mrt_m(a, 0) != 0) v = fmaf((float)mrt_m(a, 0), dm[a], v);
+        g[0] = v;
+    }
+    const float kx = sig * p.fx * 0.1f, ky = sig * p.fy * 0.1f, kz = sig * p.fz * 0.1f;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int i = 2 * m + 1;
+        float E = 0.f, O = 0.f;
+        if (cx(i) > 0) O += kx;
+        if (cx(i) < 0) O -= kx;
+        if (cy(i) > 0) O += ky;
+        if (cy(i) < 0) O -= ky;
+        if (cz(i) > 0) O += kz;
+        if (cz(i) < 0) O -= kz;
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            if (a == 0 || a == 3 || a == 5 || a == 7 || mrt_m(a, i) == 0) continue;
+            if (mrt_odd_row(a)) O = fmaf((float)mrt_m(a, i), dm[a], O);
+            else E = fmaf((float)mrt_m(a, i), dm[a], E);
+        }
+        const float gi = g[i], gb = g[i + 1];
+        g[i] = gi + E + O;
+        g[i + 1] = gb + E - O;
+    }
+    return Vel{ux, uy, uz};
+}
+
+enum { OP_TRT = 0, OP_MRT = 1 };
+
+// The collision of operator OP (SRT is TRT with equal rates).
+template <int Q, bool SCALED, int OP>
+__device__ __forceinline__ Vel collide_op(float (&g)[Q], const CollideParams &p) {
+    if constexpr (OP == OP_MRT) {
+        static_assert(Q == 19, "MRT is defined for D3Q19");
+        return collide_mrt<SCALED>(g, p);
+    } else {
+        return collide<Q, SCALED>(g, p);
+    }
 }
 
 // Shifted equilibrium of (rho, u) (Eq. 6 minus w_i).

@@ -16,7 +16,7 @@
 
 namespace slbm {
 
-template <int Q, int ST>
+template <int Q, int ST, int OP>
 __global__ void __launch_bounds__(256) pull_first_kernel(typename Store<ST>::T *__restrict__ a, int32_t S,
                                                          int32_t nf, CollideParams p) {
     using St = Store<ST>;
@@ -25,14 +25,14 @@ __global__ void __launch_bounds__(256) pull_first_kernel(typename Store<ST>::T *
     float g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = St::raw(a[i * S + k]);
-    collide<Q, St::scaled>(g, p);
+    collide_op<Q, St::scaled, OP>(g, p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) a[i * S + k] = St::pack(g[i]);
 }
 
 // pf_dist > 0: thread 0 asks the bulk-copy engine to prefetch into L2 the
 // index rows of the block pf_dist blocks ahead (about one residency wave).
-template <int Q, int ST>
+template <int Q, int ST, int OP>
 __global__ void __launch_bounds__(256) pull_step_kernel(const typename Store<ST>::T *__restrict__ src,
                                                         typename Store<ST>::T *__restrict__ dst,
                                                         const int32_t *__restrict__ P, int32_t S, int32_t nf,
@@ -56,13 +56,13 @@ __global__ void __launch_bounds__(256) pull_step_kernel(const typename Store<ST>
     g[0] = St::raw(src[k]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) g[i] = St::raw(src[e[i]]);
-    collide<Q, St::scaled>(g, p);
+    collide_op<Q, St::scaled, OP>(g, p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[i * S + k] = St::pack(g[i]);
 }
 
-template <int Q, int ST>
-static cudaError_t launch_pull_st(const Domain &d, int64_t t, cudaStream_t st) {
+template <int Q, int ST, int OP>
+static cudaError_t launch_pull_op(const Domain &d, int64_t t, cudaStream_t st) {
     using T = typename Store<ST>::T;
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
@@ -71,15 +71,23 @@ static cudaError_t launch_pull_st(const Domain &d, int64_t t, cudaStream_t st) {
     const unsigned grid = (unsigned)((nf + TH - 1) / TH);
     T *a = reinterpret_cast<T *>(d.pdf.p), *b = reinterpret_cast<T *>(d.pdf2.p);
     if (t == 0) {
-        pull_first_kernel<Q, ST><<<grid, TH, 0, st>>>(a, S, nf, p);
+        pull_first_kernel<Q, ST, OP><<<grid, TH, 0, st>>>(a, S, nf, p);
         return cudaGetLastError();
     }
     // C(t-1) sits in A at odd t, in B at even t
     const bool from_a = t & 1;
-    auto k = pull_step_kernel<Q, ST>;
+    auto k = pull_step_kernel<Q, ST, OP>;
     const int32_t pf = (int32_t)persistent_grid(k, TH, INT32_MAX);
     k<<<grid, TH, 0, st>>>(from_a ? a : b, from_a ? b : a, reinterpret_cast<const int32_t *>(d.P.p), S, nf, p, pf);
     return cudaGetLastError();
+}
+
+template <int Q, int ST>
+static cudaError_t launch_pull_st(const Domain &d, int64_t t, cudaStream_t st) {
+    if constexpr (Q == 19) {
+        if (d.op == SLBM_MRT) return launch_pull_op<Q, ST, OP_MRT>(d, t, st);
+    }
+    return launch_pull_op<Q, ST, OP_TRT>(d, t, st);
 }
 
 template <int Q>

@@ -130,8 +130,18 @@ class Domain:
 
     def set_launch(self, parity: int, threads: int, cells: int, variant: int = 0):
         """variant 0: `cells` consecutive cells per thread; variant 1: persistent
-        CTAs of `threads`-cell tiles with `cells` bulk-staged tiles in flight."""
+        CTAs of `threads`-cell tiles with `cells` bulk-staged tiles in flight;
+        odd step: variant 2 L2 index prefetch, 3 re-read slots, 4 16-bit codes."""
         A.check(A.lib().sparse_lbm_set_launch(self.h, parity, threads, cells, variant))
+
+    def set_mrt_rates(self, rates):
+        """MRT domains: the 19 per-moment relaxation rates (basis order rho, e,
+        eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx,
+        my, mz; conserved entries ignored)."""
+        r = np.ascontiguousarray(rates, np.float64)
+        if r.shape != (19,):
+            raise ValueError("19 rates")
+        A.check(A.lib().sparse_lbm_set_mrt_rates(self.h, r.ctypes.data))
 
     def set_checked(self, on: bool):
         A.check(A.lib().sparse_lbm_set_checked(self.h, int(bool(on))))
