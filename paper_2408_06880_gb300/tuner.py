@@ -21,7 +21,8 @@ import numpy as np
 from . import _capi as A
 
 EVEN_SHAPES = [(64, 1, 0), (64, 2, 0), (128, 2, 0), (64, 4, 0), (128, 2, 1), (128, 4, 1), (64, 2, 1)]
-ODD_SHAPES = [(64, 1, 0), (128, 1, 0), (96, 1, 0), (128, 2, 1), (128, 4, 1), (64, 2, 1)]
+ODD_SHAPES = [(128, 1, 2), (64, 1, 2), (256, 1, 2), (128, 1, 3), (128, 1, 4), (64, 1, 4), (128, 1, 0),
+              (128, 2, 1)]
 POOL_SHAPES = [(64, 0), (64, 8), (128, 4), (96, 4)]
 
 _lock = threading.Lock()
@@ -59,8 +60,14 @@ def size_class(n_fluid: int) -> int:
     return int(math.log2(max(n_fluid, 1)))
 
 
-def _valid(storage: int, shape) -> bool:
-    return not (shape[2] == 1 and storage == A.BF16)
+def _valid(info: dict, parity: int, shape) -> bool:
+    """Shapes the library accepts for this domain: no bulk-staged BF16; MRT
+    runs variants 0 and 2 with at most 2 cells per thread."""
+    if shape[2] == 1 and info["storage"] == A.BF16:
+        return False
+    if info["op"] == A.MRT:
+        return shape[2] in (0, 2) and shape[1] <= 2
+    return True
 
 
 def _time_parity(dom, parity: int, shape, reps: int, stream) -> float:
@@ -87,7 +94,10 @@ def tune_domain(dom, reps: int = 9, use_cache: bool = True, stream=None) -> dict
     state is saved before timing and restored afterwards."""
     import torch
     info = dom.info
-    key_base = f"{_gpu_name()}|q{info['q']}|st{info['storage']}|n{size_class(info['n_fluid'])}"
+    if info["layout"] != A.SPARSE:
+        return {}                      # the pull and dense layouts have one launch shape
+    key_base = (f"{_gpu_name()}|q{info['q']}|op{info['op']}|st{info['storage']}"
+                f"|n{size_class(info['n_fluid'])}")
     with _lock:
         cache = _load() if use_cache else {}
     chosen = {}
@@ -105,7 +115,7 @@ def tune_domain(dom, reps: int = 9, use_cache: bool = True, stream=None) -> dict
         state, step = dom.get_state()
         for parity, key in todo:
             shapes = EVEN_SHAPES if parity == 0 else ODD_SHAPES
-            res = {s: _time_parity(dom, parity, s, reps, st) for s in shapes if _valid(info["storage"], s)}
+            res = {s: _time_parity(dom, parity, s, reps, st) for s in shapes if _valid(info, parity, s)}
             best = min(res, key=res.get)
             chosen[parity] = best
             cache[key] = {"shape": list(best), "ms": res[best],
