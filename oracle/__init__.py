@@ -63,7 +63,7 @@ class _Problem(C.Structure):
                 ("flags", C.c_void_p), ("periodic", C.c_uint32), ("q", C.c_int32),
                 ("op", C.c_int32), ("omega_plus", C.c_double), ("omega_minus", C.c_double),
                 ("force", C.c_double * 3), ("inlet_u", C.c_void_p), ("rho_out", C.c_double),
-                ("mrt_s", C.c_double * 19)]
+                ("mrt_s", C.c_double * 19), ("order", C.c_int32)]
 
 
 def lib():
@@ -138,6 +138,7 @@ class Problem:
     inlet_u: np.ndarray | None = None
     rho_out: float = 1.0
     mrt_rates: tuple | None = None    # MRT: 19 per-moment rates (default mrt_default_rates)
+    order: int = 0                    # cell order: 0 lexicographic, 1 brick-8
 
     @classmethod
     def from_geometry(cls, g, **kw):
@@ -173,7 +174,7 @@ class Problem:
         rates = self.mrt_rates if self.mrt_rates is not None else mrt_default_rates(self.omega_plus)
         s = _Problem(nx, ny, nz, _ptr(self._flags_c), self.periodic, self.q, self.op,
                      self.omega_plus, self.omega_minus, (C.c_double * 3)(*self.force),
-                     _ptr(self._inlet_c), self.rho_out, (C.c_double * 19)(*rates))
+                     _ptr(self._inlet_c), self.rho_out, (C.c_double * 19)(*rates), self.order)
         self._cs = s
         return C.byref(s)
 
@@ -249,7 +250,8 @@ def stride_of(nf: int) -> int:
 
 
 def compact(p: Problem):
-    """Compacted fluid-cell order (Sec. 3.1): (cell_id[N], cell_voxel[N_F])."""
+    """Compacted fluid-cell order (Sec. 3.1), lexicographic or brick-8 by
+    `p.order`: (cell_id[N], cell_voxel[N_F])."""
     cid = np.zeros(p.n, np.int32)
     cvx = np.zeros(max(p.n, 1), np.int32)
     nf = lib().orc_compact(p._c(), _ptr(cid), _ptr(cvx))

@@ -66,6 +66,7 @@ typedef struct {
     const double *inlet_u;     /* 3 per inlet voxel, ascending voxel order; may be NULL */
     double rho_out;            /* outlet density */
     double mrt_s[19];          /* ORC_MRT (D3Q19): relaxation rate of each moment of the basis below */
+    int32_t order;             /* cell order: 0 lexicographic, 1 brick-8 (see orc_compact) */
 } orc_problem;
 
 /* ---------------------------------------------------------------- stencil */
@@ -378,17 +379,34 @@ void orc_sparse_macroscopic(const orc_problem *p, const double *f, int64_t nf, i
 /* Compacted fluid-cell order (Sec. 3.1): fluid voxels numbered in
  * ascending linear voxel id (lexicographic, x fastest).  cell_id[v] = k or
  * -1; cell_voxel[k] = v.  Returns N_F. */
+/* Compacted fluid-cell order (Sec. 3.1).  order 0: voxels lexicographic,
+ * x fastest.  order 1 ("brick-8"): the box is cut into 8x8x8 bricks taken in
+ * lexicographic brick order, and the voxels of each brick lexicographically
+ * (bricks at the high faces may be partial).  Fluid voxels are numbered in
+ * that visiting order. */
+static void visit(const orc_problem *p, int64_t v, int64_t *k, int32_t *cell_id, int32_t *cell_voxel) {
+    if (p->flags[v] == ORC_FLUID) {
+        cell_id[v] = (int32_t)*k;
+        cell_voxel[*k] = (int32_t)v;
+        ++*k;
+    } else {
+        cell_id[v] = -1;
+    }
+}
+
 int64_t orc_compact(const orc_problem *p, int32_t *cell_id, int32_t *cell_voxel) {
     int64_t n = nvox(p), k = 0;
-    for (int64_t v = 0; v < n; ++v) {
-        if (p->flags[v] == ORC_FLUID) {
-            cell_id[v] = (int32_t)k;
-            cell_voxel[k] = (int32_t)v;
-            ++k;
-        } else {
-            cell_id[v] = -1;
-        }
+    if (p->order == 0) {
+        for (int64_t v = 0; v < n; ++v) visit(p, v, &k, cell_id, cell_voxel);
+        return k;
     }
+    for (int bz = 0; bz < p->nz; bz += 8)
+        for (int by = 0; by < p->ny; by += 8)
+            for (int bx = 0; bx < p->nx; bx += 8)
+                for (int z = bz; z < bz + 8 && z < p->nz; ++z)
+                    for (int y = by; y < by + 8 && y < p->ny; ++y)
+                        for (int x = bx; x < bx + 8 && x < p->nx; ++x)
+                            visit(p, x + (int64_t)p->nx * (y + (int64_t)p->ny * z), &k, cell_id, cell_voxel);
     return k;
 }
 

@@ -17,16 +17,27 @@ DIRS27 = DIRS19 + [(1, 1, 1), (-1, -1, -1), (1, 1, -1), (-1, -1, 1), (1, -1, 1),
                    (-1, 1, 1), (1, -1, -1)]
 
 
-def brute_force_lists(g, q):
+def visiting_order(nx, ny, nz, brick):
+    """Voxels (x, y, z) in cell-numbering order: lexicographic, or brick-8
+    (8^3 bricks lexicographic, voxels lexicographic inside each brick)."""
+    if not brick:
+        return [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx)]
+    out = []
+    for bz in range(0, nz, 8):
+        for by in range(0, ny, 8):
+            for bx in range(0, nx, 8):
+                for z in range(bz, min(bz + 8, nz)):
+                    for y in range(by, min(by + 8, ny)):
+                        for x in range(bx, min(bx + 8, nx)):
+                            out.append((x, y, z))
+    return out
+
+
+def brute_force_lists(g, q, brick=0):
     dirs = DIRS19 if q == 19 else DIRS27
     nz, ny, nx = g.flags.shape
     fl = g.flags
-    order = []
-    for z in range(nz):
-        for y in range(ny):
-            for x in range(nx):
-                if fl[z, y, x] == G.FLUID:
-                    order.append((x, y, z))
+    order = [(x, y, z) for x, y, z in visiting_order(nx, ny, nz, brick) if fl[z, y, x] == G.FLUID]
     index = {v: k for k, v in enumerate(order)}
     nf = len(order)
     S = (nf + 127) // 128 * 128
@@ -72,16 +83,22 @@ CASES = [
 ]
 
 
+BRICK_CASES = [
+    ("brick_periodic", lambda s: G.random_solids((19, 10, 17), 0.35, s, periodic=7)),
+    ("brick_mixed_bc", lambda s: _mixed_geometry(s)),
+]
+
+
 @pytest.mark.parametrize("q", [19, 27])
-@pytest.mark.parametrize("name,make", CASES)
-def test_lists_match_brute_force(q, name, make):
+@pytest.mark.parametrize("name,make,brick", [c + (0,) for c in CASES] + [c + (1,) for c in BRICK_CASES])
+def test_lists_match_brute_force(q, name, make, brick):
     c, _, _ = O.stencil(q)
     assert [tuple(v) for v in c] == (DIRS19 if q == 19 else DIRS27)
     for seed in range(3):
         g = make(seed)
-        p = O.Problem.from_geometry(g, q=q)
+        p = O.Problem.from_geometry(g, q=q, order=brick)
         L = O.pull_list(p)
-        order, S, P, links = brute_force_lists(g, q)
+        order, S, P, links = brute_force_lists(g, q, brick)
         nz, ny, nx = g.flags.shape
         assert L.n_fluid == len(order) and L.stride == S
         assert np.array_equal(L.cell_voxel, [x + nx * (y + ny * z) for x, y, z in order])
@@ -137,14 +154,16 @@ SPARSE_DENSE = [
     ("periodic_srt", lambda: G.random_solids(8, 0.3, 11, periodic=7), O.SRT),
     ("walled_trt", lambda: G.random_solids(8, 0.25, 12, periodic=0b011, walls_z=True), O.TRT),
     ("mixed_bc_trt", lambda: _mixed_geometry(13), O.TRT),
+    ("partial_bricks_trt", lambda: G.random_solids((19, 10, 17), 0.3, 14, periodic=0b101), O.TRT),
 ]
 
 
+@pytest.mark.parametrize("brick", [0, 1])
 @pytest.mark.parametrize("q", [19, 27])
 @pytest.mark.parametrize("name,make,op", SPARSE_DENSE)
-def test_sparse_equals_dense_bitwise(q, name, make, op):
+def test_sparse_equals_dense_bitwise(q, name, make, op, brick):
     g = make()
-    p = O.Problem.from_geometry(g, q=q, op=op, force=(1e-5, -2e-6, 3e-6))
+    p = O.Problem.from_geometry(g, q=q, op=op, force=(1e-5, -2e-6, 3e-6), order=brick)
     rng = np.random.default_rng(5)
     n = p.n
     rho = 1.0 + rng.uniform(-0.01, 0.01, n)
