@@ -64,6 +64,8 @@ def parse():
                     help="PDF storage of the timed domains (the headline metric is FP32)")
     ap.add_argument("--shape-even", default=None, help="threads,cells,variant of the even kernel")
     ap.add_argument("--shape-odd", default=None, help="threads,cells,variant of the odd kernel")
+    ap.add_argument("--cell-order", choices=["lex", "brick8"], default="lex",
+                    help="compacted cell order of the timed domains")
     ap.add_argument("--mode", default="kernel", choices=["kernel", "serve"],
                     help="kernel: the porosity sweep (default); serve: the permeability-request stream")
     ap.add_argument("--requests", type=int, default=64, help="serve mode: number of requests")
@@ -158,7 +160,8 @@ def run_ours(a, rank, world):
     for phi in a.porosities:
         g = geometry_for(phi, a.size)
         d = P.Domain(g.flags, periodic=7, q=Q, op=P.TRT, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
-                     storage=storage, scale_exp=P.auto_scale_exp(1e-3), stream=stream)
+                     storage=storage, scale_exp=P.auto_scale_exp(1e-3), stream=stream,
+                     cell_order=P.ORDER_BRICK8 if a.cell_order == "brick8" else P.ORDER_LEX)
         apply_shapes(d, a)
         doms.append((phi, g, d))
     half = a.lbm_steps // 2
@@ -243,7 +246,7 @@ def run_ours(a, rank, world):
            "config": {"workload": f"{a.size}^3 periodic Boolean sphere packings, porosity "
                                   f"{'/'.join(str(p) for p in a.porosities)}, D3Q19 TRT magic 3/16, tau 0.8, "
                                   f"F=1e-6 x, {a.storage.upper()} PDFs",
-                      "lbm_steps_per_step": a.lbm_steps, "domains": len(doms),
+                      "lbm_steps_per_step": a.lbm_steps, "domains": len(doms), "cell_order": a.cell_order,
                       "l2": "inputs larger than L2 (PDF-list >= 0.38 GB per domain), no flush",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "roofline": roofline, "per_porosity": per, "clocks": clk, "gpu_launches": n_launch}

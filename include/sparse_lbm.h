@@ -63,6 +63,7 @@ enum { SLBM_SRT = 0, SLBM_TRT = 1, SLBM_MRT = 2 };
 enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
 enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1, SLBM_LAYOUT_SPARSE_PULL = 2 };
 enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
+enum { SLBM_ORDER_LEX = 0, SLBM_ORDER_BRICK8 = 1 };
 enum { SLBM_ORDER_CELLS = 0, SLBM_ORDER_VOXELS = 1 };
 
 /* Problem description (Sec. 2 parameters, Sec. 3 geometry). */
@@ -83,7 +84,11 @@ typedef struct {
     int32_t layout;            /* SLBM_LAYOUT_SPARSE (the method: one field, AA pattern),
                                   SLBM_LAYOUT_DENSE (comparator) or SLBM_LAYOUT_SPARSE_PULL
                                   (comparison scheme: the same lists, two fields, pull) */
-    int32_t reserved;          /* must be 0 */
+    int32_t order;             /* compacted cell order (Sec. 3.1 numbers cells row-wise):
+                                  SLBM_ORDER_LEX, lexicographic with x fastest (default), or
+                                  SLBM_ORDER_BRICK8, 8x8x8 bricks in lexicographic brick order
+                                  and voxels lexicographic inside each brick (partial bricks at
+                                  the high faces); sparse and pull layouts (dense: LEX only) */
 } slbm_desc;
 
 /* SLBM_MRT -- multiple-relaxation-time collision (D3Q19 only; the paper

@@ -14,6 +14,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EDIVERGED, ETIMEOUT, EABORTED, EDEVICE 
 SRT, TRT, MRT = 0, 1, 2
 FP32, FP16, BF16 = 0, 1, 2
 SPARSE, DENSE, SPARSE_PULL = 0, 1, 2
+ORDER_LEX, ORDER_BRICK8 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 ORDER_CELLS, ORDER_VOXELS = 0, 1
 NOALLOC_MAX_VOXELS = 268435456
@@ -33,7 +34,7 @@ class Desc(C.Structure):
                 ("omega_plus", C.c_double), ("trt_magic", C.c_double), ("force", C.c_double * 3),
                 ("inlet_u", C.c_void_p), ("n_inlet_u", C.c_int64), ("rho_out", C.c_double),
                 ("storage", C.c_int32), ("scale_exp", C.c_int32), ("layout", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("order", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

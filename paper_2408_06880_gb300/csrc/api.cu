@@ -223,7 +223,9 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (s.scale_exp < -40 || s.scale_exp > 40) return err(SLBM_EINVAL, "scale_exp must lie in [-40, 40]");
     if (s.layout != SLBM_LAYOUT_SPARSE && s.layout != SLBM_LAYOUT_DENSE && s.layout != SLBM_LAYOUT_SPARSE_PULL)
         return err(SLBM_EINVAL, "bad layout");
-    if (s.reserved != 0) return err(SLBM_EINVAL, "reserved must be 0");
+    if (s.order != SLBM_ORDER_LEX && s.order != SLBM_ORDER_BRICK8) return err(SLBM_EINVAL, "order must be 0 or 1");
+    if (s.order != SLBM_ORDER_LEX && s.layout == SLBM_LAYOUT_DENSE)
+        return err(SLBM_EUNSUPPORTED, "the dense layout has no cell order");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(s.force[a])) return err(SLBM_EINVAL, "force must be finite");
     if (!(s.rho_out > 0.0 && std::isfinite(s.rho_out))) return err(SLBM_EINVAL, "rho_out must be > 0");
@@ -261,6 +263,7 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     d.op = s.op;
     d.storage = s.storage;
     d.layout = s.layout;
+    d.order = s.order;
     d.scale_exp = s.storage == SLBM_FP32 ? 0 : s.scale_exp;
     d.omega_p = s.omega_plus;
     d.magic = s.trt_magic;

@@ -49,6 +49,7 @@ struct Domain {
     uint32_t periodic = 0;
     int64_t n_vox = 0;
     int32_t q = 19, op = SLBM_SRT, storage = SLBM_FP32, layout = SLBM_LAYOUT_SPARSE, scale_exp = 0;
+    int32_t order = SLBM_ORDER_LEX;    // compacted cell order
     double omega_p = 1.0, omega_m = 1.0, magic = 0.1875, force[3] = {0, 0, 0}, rho_out = 1.0;
     double mrt_rates[19] = {};         // MRT: rate of each basis moment
     // sizes

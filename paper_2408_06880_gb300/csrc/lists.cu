@@ -128,6 +128,35 @@ struct FluidCompaction {           // cell order (Sec. 3.1)
     }
 };
 
+// Brick-8 cell order: scan position pos = brick * 512 + local, bricks of
+// 8x8x8 voxels in lexicographic brick order, voxels lexicographic inside a
+// brick; positions outside the box (partial bricks at the high faces) are
+// skipped.
+struct BrickCompaction {
+    const uint8_t *flags;
+    int32_t *cell_id, *cell_voxel;
+    int32_t nx, ny, nz, nbx, nby;
+    __device__ int64_t voxel(int64_t pos) const {
+        const int64_t b = pos >> 9;
+        const int l = (int)(pos & 511);
+        const int x = (int)(b % nbx) * 8 + (l & 7);
+        const int y = (int)((b / nbx) % nby) * 8 + ((l >> 3) & 7);
+        const int z = (int)(b / ((int64_t)nbx * nby)) * 8 + (l >> 6);
+        if (x >= nx || y >= ny || z >= nz) return -1;
+        return x + (int64_t)nx * (y + (int64_t)ny * z);
+    }
+    __device__ int32_t value(int64_t pos) const {
+        const int64_t v = voxel(pos);
+        return v >= 0 && flags[v] == FLAG_FLUID;
+    }
+    __device__ void emit(int64_t pos, int32_t val, int32_t ex) const {
+        const int64_t v = voxel(pos);
+        if (v < 0) return;
+        cell_id[v] = val ? ex : -1;
+        if (val) cell_voxel[ex] = (int32_t)v;
+    }
+};
+
 struct InletList {                 // ascending voxel ids of inlet voxels
     const uint8_t *flags;
     int32_t *inlet_voxel;
@@ -311,7 +340,16 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
     if (cx.alloc(cell_id, N * sizeof(int32_t)) || cx.alloc(d.cell_voxel, std::max<int64_t>(N, 1) * sizeof(int32_t)))
         return -1;
     int64_t nf = 0;
-    if (scan_run(cx, FluidCompaction{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p}, N, &nf)) return -1;
+    if (d.order == SLBM_ORDER_BRICK8) {
+        const int32_t nbx = (d.nx + 7) / 8, nby = (d.ny + 7) / 8, nbz = (d.nz + 7) / 8;
+        const int64_t positions = (int64_t)nbx * nby * nbz * 512;
+        if (scan_run(cx, BrickCompaction{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p, d.nx, d.ny, d.nz,
+                                         nbx, nby},
+                     positions, &nf))
+            return -1;
+    } else if (scan_run(cx, FluidCompaction{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p}, N, &nf)) {
+        return -1;
+    }
     d.n_fluid = nf;
     d.S = (nf + 127) / 128 * 128;
     if ((int64_t)d.q * d.S >= ((int64_t)1 << 31)) {

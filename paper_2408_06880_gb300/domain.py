@@ -56,7 +56,8 @@ class Domain:
     def __init__(self, flags: np.ndarray, *, periodic: int = 7, q: int = 19, op: int = A.SRT,
                  omega: float = 1.25, trt_magic: float = 3.0 / 16.0, force=(0.0, 0.0, 0.0),
                  inlet_u: np.ndarray | None = None, rho_out: float = 1.0, storage: int = A.FP32,
-                 scale_exp: int = 0, layout: int = A.SPARSE, stream=None, allocator="torch"):
+                 scale_exp: int = 0, layout: int = A.SPARSE, stream=None, allocator="torch",
+                 cell_order: int = A.ORDER_LEX):
         L = A.lib()
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
         if flags.ndim != 3:
@@ -74,10 +75,11 @@ class Domain:
         d.inlet_u = None if self._inlet is None else self._inlet.ctypes.data
         d.n_inlet_u = 0 if self._inlet is None else self._inlet.shape[0]
         d.rho_out = rho_out
-        d.storage, d.scale_exp, d.layout, d.reserved = storage, scale_exp, layout, 0
+        d.storage, d.scale_exp, d.layout, d.order = storage, scale_exp, layout, cell_order
         self.desc = d
         self.params = dict(q=q, op=op, omega=omega, trt_magic=trt_magic, force=tuple(force),
-                           storage=storage, scale_exp=scale_exp, layout=layout, periodic=periodic)
+                           storage=storage, scale_exp=scale_exp, layout=layout, periodic=periodic,
+                           cell_order=cell_order)
         self.shape = (nx, ny, nz)
         self._alloc = TorchAllocator() if allocator == "torch" else None
         self._stream = stream

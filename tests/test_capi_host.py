@@ -58,7 +58,7 @@ def _desc(capi, flags, **kw):
 
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("q", 15), ("op", 3), ("omega_plus", 0.0), ("omega_plus", 2.0), ("storage", 3),
-    ("scale_exp", 41), ("layout", 3), ("reserved", 1), ("trt_magic", -1.0), ("rho_out", 0.0),
+    ("scale_exp", 41), ("layout", 3), ("order", 2), ("trt_magic", -1.0), ("rho_out", 0.0),
 ])
 def test_invalid_descriptors_are_rejected(capi, field, value):
     flags = np.zeros((4, 4, 4), np.uint8)
