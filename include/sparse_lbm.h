@@ -267,9 +267,9 @@ void sparse_lbm_free(slbm_t *h);
  * results out; the call makes no cudaMalloc, cudaFree or other allocating
  * library call.
  *
- * What it computes: the same compaction sparse_lbm_create uses (Sec. 3.1):
- * cell_id[v] = rank of voxel v among fluid voxels (flag 0) in ascending voxel
- * id, or -1; cell_voxel[k] = voxel id of fluid cell k; *n_fluid = count.
+ * What it computes: the compaction sparse_lbm_create uses in the
+ * lexicographic order SLBM_ORDER_LEX (Sec. 3.1): cell_id[v] = rank of voxel v
+ * among fluid voxels (flag 0) in ascending voxel id, or -1; cell_voxel[k] = voxel id of fluid cell k; *n_fluid = count.
  * All pointers are DEVICE pointers: flags[n_voxels] (uint8), cell_id[n_voxels],
  * cell_voxel[capacity >= number of fluid voxels], n_fluid[1] (int32).  The work
  * is enqueued on `stream` (cudaStream_t or NULL) and the call returns without
@@ -293,15 +293,18 @@ slbm_status sparse_lbm_compact_noalloc(const uint8_t *flags, int64_t n_voxels, i
 const char *sparse_lbm_last_error(void);
 
 /* ---- batching: many domains stepped by one persistent kernel ----------------
- * A pool steps every member domain through one launch per time step: the
- * members' compacted cell lists are concatenated through a device domain table
- * (per-domain tile offset, stride, parity, rates, force, link maps) that a
- * persistent grid walks tile by tile, so many small domains share the GPU in
- * one launch, each at its own AA parity (Sec. 5.1).  Members keep their own
- * memory and handles; all must share q and storage.  The per-cell arithmetic
- * is the single-domain kernels', so a member's state evolves bit for bit as it
- * would alone.  Pool work runs on the pool's stream: synchronise it (any pool
- * call that returns host data does) before using a member handle directly. */
+ * A pool steps many member domains together.  Members below a cell threshold
+ * (slbm_pool_set_split) are batched: their compacted cell lists are
+ * concatenated through a device domain table (per-domain tile offset, stride,
+ * parity, rates, force, link maps) and one launch per time step covers a
+ * group of them (slbm_pool_set_group_bytes), each at its own AA parity
+ * (Sec. 5.1).  Larger members run their own single-domain kernels in the same
+ * sequence, optionally on extra streams (slbm_pool_set_streams).  Members keep
+ * their own memory and handles; all must share q and storage and use the
+ * sparse layout with SRT/TRT.  The per-cell arithmetic is the single-domain
+ * kernels', so a member's state evolves bit for bit as it would alone.  Pool
+ * work runs on the pool's stream: synchronise it (any pool call that returns
+ * host data does) before using a member handle directly. */
 slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream,
                              slbm_pool_t **out);
 /* Add a domain (not owned by the pool) to a free slot; SLBM_ENOMEM if full. */
@@ -309,8 +312,9 @@ slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot);
 /* Remove a member after its queued pool work has finished (synchronises). */
 slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot);
 /* k >= 0 steps on every member (each at its own parity); use_graph != 0
- * replays a CUDA graph of the k launches, captured once per k and kept valid
- * across membership changes (the table is rewritten instead). */
+ * replays CUDA graphs: one of the batched groups' k launches (captured again
+ * when the batched table changes) and each large member's own graph of k
+ * steps (kept across membership changes). */
 slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph);
 /* out: 5 doubles per slot (capacity x 5, layout as sparse_lbm_reduce), device
  * or host; free slots are zero.  Bit-identical to sparse_lbm_reduce of each
