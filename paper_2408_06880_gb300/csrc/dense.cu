@@ -6,6 +6,8 @@
 // id.  A per-voxel 32-bit mask carries bit 31 = fluid and bit i = "the pull
 // neighbour x - c_i is a wall (or outside a non-periodic face)".  Inlet and
 // outlet voxels are not supported by this comparator.
+#include <type_traits>
+
 #include "aa_kernels.cuh"
 #include "internal.h"
 
@@ -44,45 +46,81 @@ __global__ void dense_mask_kernel(const uint8_t *flags, int32_t nx, int32_t ny, 
     mask[v] = m;
 }
 
-template <int Q, int ST>
+// Slot arithmetic in 32 bits unless Q * S reaches 2^31 (WIDE).
+template <bool WIDE>
+using SlotT = typename std::conditional<WIDE, int64_t, int32_t>::type;
+
+// Even step, two consecutive voxels per thread with vector loads and stores.
+// A pair with at least one fluid voxel is updated whole: the solid voxel's
+// slots are never read by a fluid neighbour (its mask bits send the
+// neighbour to its own slots) nor by the read-outs, so writing them is
+// harmless and keeps the accesses vectorised.
+template <int Q, int ST, bool WIDE>
 __global__ void __launch_bounds__(128) dense_even_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                          const uint32_t *__restrict__ mask, int64_t S, int32_t n,
                                                          CollideParams p) {
     using St = Store<ST>;
-    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n || !(mask[v] >> 31)) return;
-    float g[Q];
+    using T = typename St::T;
+    using I = SlotT<WIDE>;
+    const int32_t v0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (v0 >= n) return;
+    const bool two = v0 + 1 < n;
+    const uint32_t m0 = mask[v0], m1 = two ? mask[v0 + 1] : 0u;
+    if (!((m0 | m1) >> 31)) return;
+    const I s = (I)S;
+    float g[2][Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = St::raw(pdf[i * S + v]);
-    collide<Q, St::scaled>(g, p);
+    for (int i = 0; i < Q; ++i) {
+        float f[2];
+        if (two) {
+            RowIO<ST, 2>::load(pdf + (I)i * s + v0, f);
+        } else {
+            f[0] = St::raw(pdf[(I)i * s + v0]);
+            f[1] = 0.f;
+        }
+        g[0][i] = f[0];
+        g[1][i] = f[1];
+    }
+    collide<Q, St::scaled>(g[0], p);
+    collide<Q, St::scaled>(g[1], p);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) pdf[inv(i) * S + v] = St::pack(g[i]);
+    for (int i = 0; i < Q; ++i) {
+        T *dst = pdf + (I)inv(i) * s + v0;
+        if (two) {
+            const float f[2] = {g[0][i], g[1][i]};
+            st_vec<T, 2>(dst, RowIO<ST, 2>::pack(f));
+        } else {
+            dst[0] = St::pack(g[0][i]);
+        }
+    }
 }
 
 // grid (ceil(nx/blockDim), ny, nz): no divisions to find the coordinates.
-template <int Q, int ST>
+template <int Q, int ST, bool WIDE>
 __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                         const uint32_t *__restrict__ mask, int64_t S, int32_t nx,
                                                         int32_t ny, int32_t nz, CollideParams p) {
     using St = Store<ST>;
+    using I = SlotT<WIDE>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
     const int32_t v = x + nx * (y + ny * z);
     const uint32_t m = mask[v];
     if (!(m >> 31)) return;
-    int64_t R[Q];
+    const I s = (I)S;
+    I R[Q];
     float g[Q];
     g[0] = St::raw(pdf[v]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (m >> i & 1u) {
-            R[i] = i * S + v;
+            R[i] = (I)i * s + v;
         } else {
             int xn = x - cx(i), yn = y - cy(i), zn = z - cz(i);
             xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
             yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
             zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-            R[i] = inv(i) * S + xn + nx * (yn + ny * zn);
+            R[i] = (I)inv(i) * s + (I)(xn + nx * (yn + ny * zn));
         }
         g[i] = St::raw(pdf[R[i]]);
     }
@@ -108,11 +146,15 @@ static cudaError_t dense_step_t(const Domain &d, int parity, cudaStream_t st) {
     const CollideParams p = d.collide_params();
     T *pdf = (T *)d.pdf.p;
     const uint32_t *mask = (const uint32_t *)d.mask.p;
+    const bool wide = (int64_t)Q * d.S >= ((int64_t)1 << 31);
     if (parity == 0) {
-        dense_even_kernel<Q, ST><<<(unsigned)((d.n_vox + 127) / 128), 128, 0, st>>>(pdf, mask, d.S, (int32_t)d.n_vox, p);
+        const unsigned grid = (unsigned)((d.n_vox + 255) / 256);
+        if (wide) dense_even_kernel<Q, ST, true><<<grid, 128, 0, st>>>(pdf, mask, d.S, (int32_t)d.n_vox, p);
+        else dense_even_kernel<Q, ST, false><<<grid, 128, 0, st>>>(pdf, mask, d.S, (int32_t)d.n_vox, p);
     } else {
         const dim3 grid((unsigned)((d.nx + 127) / 128), (unsigned)d.ny, (unsigned)d.nz);
-        dense_odd_kernel<Q, ST><<<grid, 128, 0, st>>>(pdf, mask, d.S, d.nx, d.ny, d.nz, p);
+        if (wide) dense_odd_kernel<Q, ST, true><<<grid, 128, 0, st>>>(pdf, mask, d.S, d.nx, d.ny, d.nz, p);
+        else dense_odd_kernel<Q, ST, false><<<grid, 128, 0, st>>>(pdf, mask, d.S, d.nx, d.ny, d.nz, p);
     }
     return cudaGetLastError();
 }

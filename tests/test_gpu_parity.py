@@ -254,6 +254,34 @@ def test_dense_comparator_parity():
     assert abs(s[4] - u_o[m, 0].sum()) <= 1e-5 * np.abs(u_o[m, 0]).sum()
 
 
+def _dense_vs_sparse(g, steps_list, storage=P.FP32, q=19):
+    kw = dict(q=q, op=P.TRT, force=(1e-5, -2e-6, 0.0), storage=storage, scale_exp=16)
+    m = fluid_mask(g)
+    with gpu_domain(g, layout=P.DENSE, **kw) as dn, gpu_domain(g, **kw) as sp:
+        for n in steps_list:
+            dn.step(n)
+            sp.step(n)
+            rd, ud = dn.macroscopic(P.ORDER_VOXELS)
+            rs, us = sp.macroscopic(P.ORDER_VOXELS)
+            assert np.array_equal(rd[m], rs[m]) and np.array_equal(ud[:, m], us[:, m])
+
+
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16])
+def test_dense_comparator_is_bitwise_the_sparse_result(storage):
+    # the same collision on the same values, whatever the addressing: every
+    # fluid voxel's fields agree bit for bit at odd and even step counts
+    # (odd box width: a thread's voxel pair straddles rows and the tail)
+    g = G.random_solids((21, 16, 13), 0.35, 15, periodic=0b011, walls_z=True)
+    _dense_vs_sparse(g, (1, 4, 3), storage)
+
+
+def test_dense_comparator_64_bit_slots():
+    # Q * N >= 2^31: the dense kernels switch to 64-bit slot offsets
+    g = G.random_solids((512, 512, 440), 0.5, 16, periodic=7)
+    assert 19 * g.flags.size >= 2 ** 31
+    _dense_vs_sparse(g, (1, 2))
+
+
 def test_invalid_calls_report_status():
     g = G.random_solids(8, 0.3, 1)
     with gpu_domain(g) as d:
