@@ -108,6 +108,10 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
     const uint32_t m = mask[v];
     if (!(m >> 31)) return;
     const I s = (I)S;
+    // rows away from the y and z faces (uniform over the block): the pull
+    // neighbour is v minus a per-direction offset, wrapped only in x
+    const bool interior = y > 0 && y < ny - 1 && z > 0 && z < nz - 1;
+    const int32_t nxy = nx * ny;
     I R[Q];
     float g[Q];
     g[0] = St::raw(pdf[v]);
@@ -115,6 +119,15 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
     for (int i = 1; i < Q; ++i) {
         if (m >> i & 1u) {
             R[i] = (I)i * s + v;
+        } else if (interior) {
+            int32_t n = v - cx(i);
+            if (cy(i) > 0) n -= nx;
+            if (cy(i) < 0) n += nx;
+            if (cz(i) > 0) n -= nxy;
+            if (cz(i) < 0) n += nxy;
+            if (cx(i) > 0 && x == 0) n += nx;
+            if (cx(i) < 0 && x == nx - 1) n -= nx;
+            R[i] = (I)inv(i) * s + (I)n;
         } else {
             int xn = x - cx(i), yn = y - cy(i), zn = z - cz(i);
             xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
