@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--sequential", action="store_true", help="serve mode: also time one-at-a-time solves")
     ap.add_argument("--pool-graph", type=int, default=1, help="serve mode: replay pool steps as CUDA graphs")
     ap.add_argument("--pool-streams", type=int, default=2, help="serve mode: streams of a pool step")
+    ap.add_argument("--large-cap", type=int, default=2,
+                    help="serve mode with lanes: at most this many requests in the large lane (0: no bound)")
+    ap.add_argument("--lanes", default="1000000:4",
+                    help="serve mode: 'CELLS:CHUNKS' puts requests below CELLS fluid cells in a lane that "
+                         "advances CHUNKS chunks per tick ('none': one lockstep lane)")
     ap.add_argument("--group-mb", type=float, default=None,
                     help="serve mode: L2 group size of the pool in MiB (0 = one group; default: the library's)")
     a = ap.parse_args()
@@ -513,11 +518,15 @@ def run_serve(a):
                                   f"1e-6 relative change of mean u_x per 100 steps or {a.max_steps} steps",
                       "budget_gb": a.budget_gb, "capacity": a.capacity, "arrivals": a.arrivals,
                       "pool_graph": bool(a.pool_graph), "group_mb": a.group_mb,
-                      "pool_streams": a.pool_streams,
+                      "pool_streams": a.pool_streams, "lanes": a.lanes, "large_cap": a.large_cap,
                       "parallelism": f"request replicas x{world}" if world > 1 else "single GPU"}}
+    lanes = None
+    if a.lanes != "none":
+        cells, chunks = (int(x) for x in a.lanes.split(":"))
+        lanes = ((cells, chunks), (None, 1, a.large_cap or None))
     ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph),
                      group_bytes=None if a.group_mb is None else int(a.group_mb * 2 ** 20),
-                     streams=a.pool_streams)
+                     streams=a.pool_streams, lanes=lanes)
     budget = int(a.budget_gb * 2 ** 30)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()

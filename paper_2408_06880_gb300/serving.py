@@ -73,26 +73,50 @@ def nu_of(omega: float) -> float:
 
 
 class GpuExecutor:
-    """Pool-backed executor: one `Domain` per admitted request, all stepped by
-    one `Pool`."""
+    """Pool-backed executor: one `Domain` per admitted request, stepped by
+    pools.  With `lanes` = ((max_cells, chunks[, cap]), ..., (None, chunks[,
+    cap])), a
+    request goes to the first lane whose max_cells exceeds its fluid cells;
+    each lane is a pool on its own stream, and per server tick lane l
+    advances its members `chunks` chunks, reducing their FP64 sums on the
+    device after each one (no host wait in between), while the lanes run
+    concurrently.  Small requests then progress several chunks for one of the
+    large ones -- a fairer share of GPU time than lockstep -- and the server
+    still tests convergence after every chunk, so results and step counts are
+    those of a solve alone.  `cap` bounds a lane's concurrent members (the
+    server leaves a request queued while its lane is full)."""
 
     def __init__(self, q: int = 19, storage: int = A.FP32, capacity: int = 64, scale_exp: int | None = None,
                  graph: bool = True, stream=None, pool_launch: tuple | None = None,
-                 group_bytes: int | None = None, streams: int = 2):
+                 group_bytes: int | None = None, streams: int = 2, lanes: tuple | None = None):
+        import torch
         from .domain import Domain, auto_scale_exp
         from .pool import Pool
+        self._torch = torch
         self._Domain = Domain
         self.q, self.storage, self.graph = q, storage, graph
         self.scale_exp = auto_scale_exp(1e-3) if scale_exp is None else scale_exp
         self.stream = stream
-        self.pool = Pool(q, storage, capacity, stream=stream)
-        if pool_launch:
-            self.pool.set_launch(*pool_launch)
-        if group_bytes is not None:
-            self.pool.set_group_bytes(group_bytes)
-        if streams > 1:
-            self.pool.set_streams(streams)
         self.capacity = capacity
+        spec = tuple(lanes) if lanes else ((None, 1),)
+        self.lanes = []
+        for entry in spec:
+            max_cells, chunks = entry[0], entry[1]
+            cap = entry[2] if len(entry) > 2 and entry[2] else capacity
+            st = stream if len(spec) == 1 else torch.cuda.Stream()
+            pool = Pool(q, storage, capacity, stream=st)
+            if pool_launch:
+                pool.set_launch(*pool_launch)
+            if group_bytes is not None:
+                pool.set_group_bytes(group_bytes)
+            if streams > 1:
+                pool.set_streams(streams)
+            self.lanes.append(dict(max=max_cells, chunks=int(chunks), cap=int(cap), pool=pool, stream=st,
+                                   slots=set(), buf=None))
+        self.pool = self.lanes[0]["pool"]
+        if len(self.lanes) > 1:            # the server drives lanes through launch/collect
+            self.launch = self._launch
+            self.collect = self._collect
 
     def footprint(self, req: Request) -> int:
         """Device bytes a request will hold (PDF-list, index-list, cell list,
@@ -107,21 +131,67 @@ class GpuExecutor:
                             trt_magic=req.trt_magic, force=req.force, storage=self.storage,
                             scale_exp=self.scale_exp, stream=self.stream)
 
+    def _lane_of(self, nf: int) -> int:
+        for li, lane in enumerate(self.lanes):
+            if lane["max"] is None or nf < lane["max"]:
+                return li
+        raise ValueError("no lane takes this request")
+
+    def can_admit(self, req: Request) -> bool:
+        """The request's lane has room (at most `cap` active members)."""
+        lane = self.lanes[self._lane_of(req.n_fluid)]
+        return len(lane["slots"]) < lane["cap"]
+
     def add(self, dom) -> int:
-        return self.pool.add(dom)
+        li = self._lane_of(dom.n_fluid)
+        lane = self.lanes[li]
+        s = lane["pool"].add(dom)
+        lane["slots"].add(s)
+        return li * self.capacity + s
 
     def remove(self, slot: int, dom) -> None:
-        self.pool.remove(slot)
+        li, s = divmod(slot, self.capacity)
+        self.lanes[li]["pool"].remove(s)
+        self.lanes[li]["slots"].discard(s)
         dom.close()
 
     def step(self, k: int) -> None:
-        self.pool.step(k, graph=self.graph)
+        for lane in self.lanes:
+            if lane["slots"]:
+                lane["pool"].step(k, graph=self.graph)
 
     def sums(self) -> np.ndarray:
-        return self.pool.reduce()
+        out = np.zeros((self.capacity * len(self.lanes), 5))
+        for li, lane in enumerate(self.lanes):
+            out[li * self.capacity:(li + 1) * self.capacity] = lane["pool"].reduce()
+        return out
+
+    def _launch(self, k: int) -> None:
+        torch = self._torch
+        for lane in self.lanes:
+            if not lane["slots"]:
+                continue
+            if lane["buf"] is None:
+                # filled by the pool's reductions (which clear their output) on the lane's stream
+                lane["buf"] = torch.empty((lane["chunks"], self.capacity, 5), dtype=torch.float64, device="cuda")
+            for j in range(lane["chunks"]):
+                lane["pool"].step(k, graph=self.graph)
+                lane["pool"].reduce_device(lane["buf"][j])
+
+    def _collect(self) -> dict:
+        out = {}
+        for li, lane in enumerate(self.lanes):
+            if not lane["slots"]:
+                continue
+            lane["stream"].synchronize()
+            arr = lane["buf"].cpu().numpy()
+            for s in lane["slots"]:
+                out[li * self.capacity + s] = arr[:, s, :]
+        return out
 
     def close(self) -> None:
-        self.pool.close()
+        for lane in self.lanes:
+            lane["pool"].close()
 
 
 class Server:
@@ -166,7 +236,7 @@ class Server:
                     results.append(Result(req.rid, None, 0, False, req.arrival, None, self.clock() - t0,
                                           error="footprint exceeds the whole HBM budget"))
                     continue
-                if used + need > self.budget:
+                if used + need > self.budget or (hasattr(self.ex, "can_admit") and not self.ex.can_admit(req)):
                     i += 1
                     continue
                 queue.pop(i)
@@ -195,14 +265,24 @@ class Server:
                     if wait > 0:
                         self.sleep(min(wait, 0.05))
                 continue
-            # ---- one chunk of steps for every active request
+            # ---- one chunk of steps for every active request (an executor
+            # with lanes may advance some requests several chunks, reporting
+            # the sums after each one)
             tb = self.clock()
             try:
                 if self.fault_hook:
                     self.fault_hook("step", None)
-                self.ex.step(self.chunk)
+                lanes = hasattr(self.ex, "launch")
+                if lanes:
+                    self.ex.launch(self.chunk)
+                else:
+                    self.ex.step(self.chunk)
                 admit(True)                   # overlaps the chunk in flight
-                sums = self.ex.sums()
+                if lanes:
+                    series = self.ex.collect()
+                else:
+                    sums = self.ex.sums()
+                    series = {slot: sums[slot][None, :] for slot in active}
             except A.SlbmError as e:
                 # a device-level failure ends every active request
                 for slot, st in list(active.items()):
@@ -215,36 +295,40 @@ class Server:
                 if st["fresh"]:               # joined after this chunk was launched
                     st["fresh"] = False
                     continue
-                st["steps"] += self.chunk
-                updates += st["nf"] * self.chunk
-                s = sums[slot]
-                req = st["req"]
-                err = None
-                mean_ux = s[4] / max(st["nf"], 1)
-                if not np.all(np.isfinite(s)):
-                    err = "diverged: domain sums are not finite"
-                elif abs(mean_ux) > U_MAX_STABLE:
-                    err = "diverged: mean speed above the stability bound"
-                if self.fault_hook:
-                    try:
-                        self.fault_hook("check", req.rid)
-                    except Exception as e:
-                        err = f"injected: {e}"
-                done = err is not None
-                conv = False
-                if not done:
-                    prev = st["prev"]
-                    if prev is not None and mean_ux != 0.0 and abs(mean_ux - prev) / abs(mean_ux) < req.tol:
-                        done = conv = True
-                    elif st["steps"] >= req.max_steps:
-                        done = True
-                    st["prev"] = mean_ux
-                if done:
-                    results.append(self._retire(slot, st, t0, error=err, converged=conv, sums=s))
-                    used -= st["need"]
-                    del active[slot]
+                for s in series[slot]:        # the sums after each chunk, in order
+                    st["steps"] += self.chunk
+                    updates += st["nf"] * self.chunk
+                    done, err, conv = self._check(st, s)
+                    if done:
+                        results.append(self._retire(slot, st, t0, error=err, converged=conv, sums=s))
+                        used -= st["need"]
+                        del active[slot]
+                        break
         wall = self.clock() - t0
         return results, self.stats(results, wall, busy_s, updates)
+
+    def _check(self, st, s) -> tuple[bool, str | None, bool]:
+        """Convergence / divergence test of one request after one chunk:
+        (done, error, converged)."""
+        req = st["req"]
+        err = None
+        mean_ux = s[4] / max(st["nf"], 1)
+        if not np.all(np.isfinite(s)):
+            err = "diverged: domain sums are not finite"
+        elif abs(mean_ux) > U_MAX_STABLE:
+            err = "diverged: mean speed above the stability bound"
+        if self.fault_hook:
+            try:
+                self.fault_hook("check", req.rid)
+            except Exception as e:
+                err = f"injected: {e}"
+        if err is not None:
+            return True, err, False
+        prev = st["prev"]
+        st["prev"] = mean_ux
+        if prev is not None and mean_ux != 0.0 and abs(mean_ux - prev) / abs(mean_ux) < req.tol:
+            return True, None, True
+        return st["steps"] >= req.max_steps, None, False
 
     def _retire(self, slot, st, t0, error=None, converged=False, sums=None):
         req = st["req"]

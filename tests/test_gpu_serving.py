@@ -23,11 +23,14 @@ def small_requests(n=6, tol=1e-5, max_steps=6000):
     return reqs
 
 
+@pytest.mark.parametrize("lanes", [None, ((20000, 3), (None, 1))])
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
-def test_served_results_equal_alone(storage):
+def test_served_results_equal_alone(storage, lanes):
+    # lanes: requests under 20000 cells (the 24^3 and 32^3 samples) advance
+    # three chunks per tick in their own pool, the others one
     reqs = small_requests()
     alone = {r.rid: solve_alone(r, storage=storage, scale_exp=24) for r in reqs}
-    ex = GpuExecutor(19, storage, capacity=3, scale_exp=24)     # fewer slots than requests
+    ex = GpuExecutor(19, storage, capacity=3, scale_exp=24, lanes=lanes)     # fewer slots than requests
     try:
         res, st = Server(ex, budget_bytes=1 << 34, chunk=100).run(reqs, realtime=False)
     finally:

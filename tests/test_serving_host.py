@@ -196,3 +196,78 @@ def test_realtime_arrivals_and_latency_stats():
 def test_chunk_must_be_even():
     with pytest.raises(ValueError):
         Server(FakeExecutor(), 1, chunk=7)
+
+
+class FakeLaneExecutor(FakeExecutor):
+    """Two lanes: requests below `small` cells advance `chunks` chunks per
+    tick and report the sums after each; the others one chunk."""
+
+    def __init__(self, capacity=4, small=600, chunks=4):
+        super().__init__(capacity)
+        self.small, self.chunks = small, chunks
+        self.series = {}
+
+    def _sums_of(self, d):
+        T = d.req.meta.get("T", 500.0)
+        return np.array([0, 0, 0, 0, 1e-3 * (1 - math.exp(-d.t / T)) * d.nf])
+
+    def launch(self, k):
+        self.series = {}
+        for s, d in self.slots.items():
+            n = self.chunks if d.nf < self.small else 1
+            rows = []
+            for _ in range(n):
+                d.t += k
+                rows.append(self._sums_of(d))
+            self.series[s] = np.array(rows)
+
+    def collect(self):
+        return self.series
+
+
+def test_lanes_keep_results_and_let_small_requests_finish_sooner():
+    def reqs():
+        return [req(0, n=12, T=900.0), req(1, n=8, T=300.0), req(2, n=12, T=700.0), req(3, n=8, T=500.0)]
+    alone = {}
+    for r in reqs():
+        res, _ = Server(FakeExecutor(1), 10 ** 9).run([r], realtime=False)
+        alone[r.rid] = res[0]
+    clock = FakeClock()
+    ex = FakeLaneExecutor(capacity=4, small=600, chunks=4)
+    srv = Server(ex, 10 ** 9, clock=clock, sleep=clock.sleep)
+    orig = ex.launch
+
+    def timed_launch(k):
+        orig(k)
+        clock.t += 1.0                          # one tick = one unit of time
+    ex.launch = timed_launch
+    res, st = srv.run(reqs(), realtime=False)
+    assert st["solved"] == 4
+    by = {r.rid: r for r in res}
+    for rid, r in by.items():                   # identical to a solve alone
+        assert r.steps == alone[rid].steps and r.permeability == alone[rid].permeability
+    # the 8^3 requests (512 cells) advance 4 chunks per tick: they retire after
+    # a quarter of the ticks a lockstep server would need
+    for rid in (1, 3):
+        assert by[rid].t_finish <= math.ceil(by[rid].steps / 400) + 1
+
+
+def test_lane_cap_bounds_concurrent_large_requests():
+    class Capped(FakeLaneExecutor):
+        def __init__(self):
+            super().__init__(capacity=6, small=600, chunks=2)
+            self.peak_large = 0
+
+        def can_admit(self, r):
+            large = sum(1 for d in self.slots.values() if d.nf >= self.small)
+            return r.n_fluid < self.small or large < 2
+
+        def launch(self, k):
+            self.peak_large = max(self.peak_large, sum(1 for d in self.slots.values() if d.nf >= self.small))
+            super().launch(k)
+
+    ex = Capped()
+    reqs = [req(i, n=12 if i % 2 else 8, T=300.0 + 40 * i) for i in range(8)]
+    res, st = Server(ex, 10 ** 9).run(reqs, realtime=False)
+    assert st["solved"] == 8
+    assert ex.peak_large == 2
