@@ -205,6 +205,7 @@ extern "C" {
 const char *sparse_lbm_last_error(void) { return g_msg.c_str(); }
 
 slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc, void *stream, slbm_t **out) {
+    const Range range_("slbm create");
     if (!desc || !out) return err(SLBM_EINVAL, "desc and out must be non-NULL");
     *out = nullptr;
     const slbm_desc &s = *desc;
@@ -343,6 +344,7 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
 }
 
 slbm_status sparse_lbm_step(slbm_t *h, int32_t n) {
+    const Range range_("slbm step");
     if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
     Domain &d = h->d;
     for (int32_t t = 0; t < n; ++t) {
@@ -354,6 +356,7 @@ slbm_status sparse_lbm_step(slbm_t *h, int32_t n) {
 }
 
 slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n) {
+    const Range range_("slbm step (graph)");
     if (!h || n < 0) return err(SLBM_EINVAL, "need a handle and n >= 0");
     if (n == 0) return ok();
     Domain &d = h->d;
@@ -367,6 +370,7 @@ slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n) {
 }
 
 slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t order, int32_t mem) {
+    const Range range_("slbm macroscopic");
     if (!h) return err(SLBM_EINVAL, "null handle");
     if (order != SLBM_ORDER_CELLS && order != SLBM_ORDER_VOXELS) return err(SLBM_EINVAL, "bad order");
     if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return err(SLBM_EINVAL, "bad mem");
@@ -400,6 +404,7 @@ slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t orde
 }
 
 slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem) {
+    const Range range_("slbm reduce");
     if (!h || !out) return err(SLBM_EINVAL, "null argument");
     Domain &d = h->d;
     if (mem == SLBM_MEM_DEVICE) {

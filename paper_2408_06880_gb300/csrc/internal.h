@@ -7,10 +7,20 @@
 #include <type_traits>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "sparse_lbm.h"
 
 namespace slbm {
+
+// Named NVTX range for profilers (Nsight); free when no tool is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Thread-local error record behind sparse_lbm_last_error().
 void set_error(slbm_status s, const std::string &msg);

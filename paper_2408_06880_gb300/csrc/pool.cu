@@ -725,6 +725,7 @@ slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot) {
 }
 
 slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph) {
+    const Range range_("slbm pool step");
     if (!p || k < 0) return perr(SLBM_EINVAL, "need a pool and k >= 0");
     if (k == 0) {
         set_error(SLBM_OK, "");
@@ -810,6 +811,7 @@ slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph) {
 }
 
 slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem) {
+    const Range range_("slbm pool reduce");
     if (!p || !out) return perr(SLBM_EINVAL, "null argument");
     if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return perr(SLBM_EINVAL, "bad mem");
     cudaError_t e = cudaSuccess;

@@ -11,6 +11,35 @@ import numpy as np
 from . import _capi as A
 
 
+def validate_pull_list(P: np.ndarray, n_fluid: int, n_links: int) -> None:
+    """Host-side check of a canonical pull index-list (Sec. 3.1, 3.1.1), as
+    exported by `Domain.export_lists`: rows i-1 = directions i = 1..Q-1,
+    stride S = P.shape[1].  Column k < n_fluid holds i*S + n (fluid neighbour
+    n < n_fluid), inverse(i)*S + k (wall: the cell's own inverse slot) or
+    -(b+1) with b < n_links (inlet/outlet link); padding columns hold
+    INT32_MIN.  Raises ValueError naming the first bad entry."""
+    P = np.asarray(P, np.int64)
+    q = P.shape[0] + 1
+    S = P.shape[1]
+    if S < n_fluid or S % 128:
+        raise ValueError(f"stride {S} does not hold {n_fluid} cells in multiples of 128")
+    k = np.arange(n_fluid)
+    pad = np.iinfo(np.int32).min
+    for r in range(q - 1):
+        i = r + 1
+        ib = i + 1 if i % 2 else i - 1                      # inverse pairs (i, i+1), i odd
+        e = P[r, :n_fluid]
+        fluid = (e >= i * S) & (e < i * S + n_fluid)
+        wall = e == ib * S + k
+        link = (e < 0) & (e >= -n_links)
+        bad = ~(fluid | wall | link)
+        if bad.any():
+            j = int(np.argmax(bad))
+            raise ValueError(f"direction {i}, cell {j}: entry {int(e[j])} is no fluid, wall or link slot")
+        if np.any(P[r, n_fluid:] != pad):
+            raise ValueError(f"direction {i}: a padding column is not INT32_MIN")
+
+
 class TorchAllocator:
     """Device memory for the library from PyTorch's caching allocator.
 
@@ -201,6 +230,12 @@ class Domain:
                                                 ld.ctypes.data, lt.ctypes.data))
         return dict(cell_voxel=cv[:nf], P=P[:, :S], link_cell=lc[:nl], link_dir=ld[:nl], link_type=lt[:nl],
                     n_fluid=nf, stride=S)
+
+    def validate_lists(self) -> None:
+        """Check every entry of the device's index-list on the host
+        (`validate_pull_list`)."""
+        L = self.export_lists()
+        validate_pull_list(L["P"], L["n_fluid"], int(L["link_cell"].size))
 
     def export_codes(self) -> tuple[np.ndarray, np.ndarray]:
         """The odd step's 16-bit link codes ((Q-1) x S uint16) and their

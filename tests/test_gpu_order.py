@@ -59,3 +59,10 @@ def test_brick_order_fields_equal_lexicographic(name, make, storage, layout):
             rl, ul = lex.macroscopic(P.ORDER_VOXELS)
             rb, ub = brk.macroscopic(P.ORDER_VOXELS)
             assert np.array_equal(rl, rb) and np.array_equal(ul, ub)
+
+
+@pytest.mark.parametrize("order", [P.ORDER_LEX, P.ORDER_BRICK8])
+@pytest.mark.parametrize("name,make", GEOMS)
+def test_device_lists_pass_the_host_validator(name, make, order):
+    with gpu_domain(make(), q=27, cell_order=order) as d:
+        d.validate_lists()

@@ -187,3 +187,28 @@ def test_sparse_rest_state_is_the_dense_rest_state():
     p = O.Problem.from_geometry(g, q=27)
     L = O.pull_list(p)
     assert np.array_equal(O.sparse_rest(p, L), O.sparse_from_dense(L, O.dense_init(p)))
+
+
+def test_host_list_validator_accepts_valid_and_rejects_planted_mistakes():
+    # the package's host-side validator on the oracle's lists; mistakes are
+    # planted in copies of the oracle's list
+    from paper_2408_06880_gb300.domain import validate_pull_list
+    for q in (19, 27):
+        g = _mixed_geometry(7)
+        L = O.pull_list(O.Problem.from_geometry(g, q=q))
+        nl = int(L.bc_cell.size)
+        validate_pull_list(L.P, L.n_fluid, nl)
+        S = L.stride
+        for r, k, v in ((0, 0, (q + 3) * S),            # beyond the list
+                        (2, 1, 3 * S + L.n_fluid),       # fluid column past N_F
+                        (4, 2, -(nl + 1)),               # link id out of range
+                        (1, 0, 1 * S + 0 + 5 * S)):      # wall slot of another row
+            bad = L.P.copy()
+            bad[r, k] = v
+            with pytest.raises(ValueError):
+                validate_pull_list(bad, L.n_fluid, nl)
+        bad = L.P.copy()
+        bad[0, -1] = 0                                     # padding overwritten
+        if L.n_fluid < S:
+            with pytest.raises(ValueError):
+                validate_pull_list(bad, L.n_fluid, nl)
