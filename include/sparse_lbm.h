@@ -9,8 +9,13 @@
  * replaces the lost neighbourhood information, with no-slip and periodic
  * boundaries folded into the list (Sec. 3.1.1).  Time stepping uses the in-place
  * AA pattern (Sec. 5.1): a cell-local "even" step and an index-driven "odd" step
- * on one PDF field.  The collision is SRT (Eq. 5) or TRT with the second-order
- * equilibrium (Eq. 6) and a Guo body force.
+ * on one PDF field.  The collision is SRT (Eq. 5), TRT or D3Q19 MRT with the
+ * second-order equilibrium (Eq. 6) and a Guo body force.  For the paper's
+ * comparisons the same lists also drive a two-field pull layout (Sec. 5.1),
+ * and a dense direct-addressing layout serves as the comparator (Sec. 4).
+ * Populations are stored shifted (f_i - w_i) in FP32, FP16 or BF16; cells are
+ * numbered lexicographically or in 8^3 bricks.  Pools step many domains
+ * together (batching), for the serving layer above this ABI.
  *
  * Conventions shared by every call
  *   - Every call returns an slbm_status; nothing aborts or throws across the ABI.
