@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--shape-odd", default=None, help="threads,cells,variant of the odd kernel")
     ap.add_argument("--cell-order", choices=["lex", "brick8"], default="lex",
                     help="compacted cell order of the timed domains")
-    ap.add_argument("--mode", default="kernel", choices=["kernel", "serve"],
+    ap.add_argument("--mode", default="kernel", choices=["kernel", "serve", "workloads"],
                     help="kernel: the porosity sweep (default); serve: the permeability-request stream")
     ap.add_argument("--requests", type=int, default=64, help="serve mode: number of requests")
     ap.add_argument("--max-steps", type=int, default=20000, help="serve mode: step cap per request")
@@ -580,8 +580,68 @@ def run_serve(a):
     return out
 
 
+def _time_pairs(P, d, stream, pairs):
+    import torch
+    d.step(4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(2 * pairs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (2 * pairs)            # ms per LBM step
+
+
+def run_workloads(a, pairs=10):
+    """The application-shaped workloads (stand-ins for Sec. 6.2 and 6.3):
+    the 512 x 256 x 256 particle bed (D3Q27 TRT, velocity inlet, pressure
+    outlet, FP32 and FP16) and the 1024 x 512 x 512 artery tree (D3Q19 TRT,
+    sparse, plus the dense comparator on the same voxels with the inlet and
+    outlet voxels as walls -- it supports no open boundaries): MFLUPS, GB/s
+    at the algorithmic bytes, memory per fluid cell, fluid fraction."""
+    import torch
+    import geometry as G
+    import paper_2408_06880_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.Stream()
+    peak, _ = load_peaks()
+    out = {"mode": "workloads", "data": "synthetic", "peak_gbs": peak, "rows": []}
+
+    def row(name, g, q, storage, layout=P.SPARSE, flags=None):
+        b = 4 if storage == P.FP32 else 2
+        d = P.Domain(g.flags if flags is None else flags, periodic=g.periodic,
+                     inlet_u=g.inlet_u if flags is None else None, rho_out=g.rho_out, q=q, op=P.TRT, omega=OMEGA,
+                     trt_magic=MAGIC, storage=storage, scale_exp=P.auto_scale_exp(0.06) if storage else 0,
+                     layout=layout, stream=stream)
+        ms = _time_pairs(P, d, stream, pairs)
+        nf = int(np.count_nonzero(g.flags == 0))
+        per = (2 * q * b + (q - 1) * B_IDX / 2) if layout == P.SPARSE else None
+        r = {"workload": name, "q": q, "storage": {P.FP32: "fp32", P.FP16: "fp16"}[storage],
+             "layout": {P.SPARSE: "sparse", P.DENSE: "dense"}[layout], "n_voxels": int(g.flags.size),
+             "n_fluid": nf, "fluid_fraction": round(nf / g.flags.size, 5),
+             "mflups": round(nf / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
+             "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)}
+        if per is not None:
+            gbs = nf * per / (ms / 1e3) / 1e9
+            r.update({"gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
+        d.close()
+        out["rows"].append(r)
+        print(json.dumps(r), file=sys.stderr, flush=True)
+
+    bed = G.particle_bed()
+    row("particle bed 512x256x256", bed, 27, P.FP32)
+    row("particle bed 512x256x256", bed, 27, P.FP16)
+    art = G.artery_tree()
+    row("artery tree 1024x512x512", art, 19, P.FP32)
+    walls = np.where(art.flags >= G.INLET, np.uint8(G.WALL), art.flags).astype(np.uint8)
+    row("artery tree 1024x512x512 (inlet/outlet as walls)", art, 19, P.FP32, P.DENSE, flags=walls)
+    return out
+
+
 def main():
     a = parse()
+    if a.mode == "workloads" and a.impl == "ours":
+        print(json.dumps(run_workloads(a)), flush=True)
+        return
     if a.mode == "serve" and a.impl == "ours":
         world = int(os.environ.get("WORLD_SIZE", "1"))
         if world > 1:
