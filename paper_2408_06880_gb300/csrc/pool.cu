@@ -154,28 +154,27 @@ __global__ void __launch_bounds__(128, 4) pool_step_kernel(const PoolHeader *__r
 // CTAs read before starting.
 constexpr int POOL_THREADS = 128;
 
-struct TileDesc {
-    void *pdf;
-    const int32_t *R;
-    int32_t S, nf, first, member;
+// The members of one launch (a group), passed by value as a kernel parameter
+// (constant bank): member m owns the launch's tiles first_tile[m] ..
+// first_tile[m+1]-1.  A CTA finds its member by a binary search over
+// first_tile -- no dependent global load before its cells' loads.
+constexpr int PT_MAX = 256;
+struct PoolTable {
+    int32_t n;                         // members
+    int32_t first_tile[PT_MAX + 1];    // [n] = tiles of the launch
+    void *pdf[PT_MAX];
+    const int32_t *R[PT_MAX];
+    int32_t S[PT_MAX], nf[PT_MAX], row[PT_MAX];   // row: the member's row in the pool table
 };
 
-__global__ void fill_tiles(const PoolEntry *__restrict__ tab, int32_t n_dom, int32_t cells_per_tile,
-                           const int32_t *__restrict__ begin, TileDesc *__restrict__ out) {
-    const int32_t d = blockIdx.y;
-    if (d >= n_dom) return;
-    const PoolEntry &E = tab[d];
-    const int32_t n = (E.nf + cells_per_tile - 1) / cells_per_tile, b = begin[d];
-    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        TileDesc D;
-        D.pdf = E.pdf;
-        D.R = E.R;
-        D.S = E.S;
-        D.nf = E.nf;
-        D.first = t * cells_per_tile;
-        D.member = d;
-        out[b + t] = D;
+__device__ __forceinline__ int pt_member(const PoolTable &T, int32_t t) {
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.first_tile[mid] <= t) lo = mid;
+        else hi = mid - 1;
     }
+    return lo;
 }
 
 // PARITY: 0 / 1 uniform, -1 mixed (per member, from its table row).
@@ -186,22 +185,24 @@ __global__ void fill_tiles(const PoolEntry *__restrict__ tab, int32_t n_dom, int
 // residency wave later).
 template <int Q, int ST, int PARITY, bool UNI, bool BC, int CPT>
 __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry *__restrict__ tab,
-                                                                 const TileDesc *__restrict__ tiles,
+                                                                 const __grid_constant__ PoolTable pt,
                                                                  int32_t seq_step,
                                                                  const volatile int32_t *abort_flag,
                                                                  int32_t *stop,
                                                                  const __grid_constant__ CollideParams up,
-                                                                 int32_t n_tiles, int32_t pf_dist) {
+                                                                 int32_t pf_dist) {
     using St = Store<ST>;
     using T = typename St::T;
+    constexpr int32_t TILE = POOL_THREADS * CPT;
     const int32_t t = blockIdx.x;
-    if (PARITY == 1 && pf_dist > 0 && threadIdx.x == 0 && t + pf_dist < n_tiles) {
-        const TileDesc F = tiles[t + pf_dist];
-        const int32_t left = F.nf - F.first;
+    if (PARITY == 1 && pf_dist > 0 && threadIdx.x == 0 && t + pf_dist < pt.first_tile[pt.n]) {
+        const int mf = pt_member(pt, t + pf_dist);
+        const int32_t first = (t + pf_dist - pt.first_tile[mf]) * TILE;
+        const int32_t left = pt.nf[mf] - first;
         if (left > 0) {
-            const int32_t cells = ((left < POOL_THREADS ? left : POOL_THREADS) + 3) & ~3;   // whole 16 bytes
+            const int32_t cells = ((left < TILE ? left : TILE) + 3) & ~3;   // whole 16 bytes
 #pragma unroll
-            for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(F.R + r * F.S + F.first, (uint32_t)cells * 4u);
+            for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(pt.R[mf] + r * pt.S[mf] + first, (uint32_t)cells * 4u);
         }
     }
     int32_t halt = *(volatile int32_t *)stop;
@@ -210,10 +211,14 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
         halt = 1;
     }
     if (halt) return;
-    const TileDesc D = tiles[t];
+    const int m = pt_member(pt, t);
+    struct {
+        int32_t first, member;
+        const int32_t *R;
+    } D{(t - pt.first_tile[m]) * TILE, pt.row[m], pt.R[m]};
     const CollideParams &p = UNI ? up : tab[D.member].p;
-    T *pdf = reinterpret_cast<T *>(D.pdf);
-    const int32_t S = D.S, nf = D.nf;
+    T *pdf = reinterpret_cast<T *>(pt.pdf[m]);
+    const int32_t S = pt.S[m], nf = pt.nf[m];
     int parity = PARITY;
     if (PARITY < 0) parity = (tab[D.member].parity0 + seq_step) & 1;
     if (parity == 0) {
@@ -255,8 +260,8 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
     }
 }
 
-using TileKernel = void (*)(const PoolEntry *, const TileDesc *, int32_t, const volatile int32_t *, int32_t *,
-                            const CollideParams, int32_t, int32_t);
+using TileKernel = void (*)(const PoolEntry *, const PoolTable, int32_t, const volatile int32_t *, int32_t *,
+                            const CollideParams, int32_t);
 
 // mode: 0 mixed parity, 1 + 2*parity + uni
 template <int Q, int ST>
@@ -316,10 +321,7 @@ struct slbm_pool {
     std::vector<int32_t> order;          // slot of each table row
     PoolHeader host_hdr{0, 0};
     void *d_tab = nullptr, *d_hdr = nullptr, *d_status = nullptr, *d_red = nullptr;
-    TileDesc *d_tiles[2] = {nullptr, nullptr};   // tile descriptors: [0] 256-cell, [1] 128-cell tiles
-    int64_t tiles_cap[2] = {0, 0};
-    int32_t n_tiles[2] = {0, 0};
-    int32_t *d_begin = nullptr;                  // per-row first tile (scratch for the fill)
+    std::vector<PoolTable> ptab;                 // per group: [2g] 256-cell, [2g+1] 128-cell tiling
     int32_t *h_abort = nullptr;          // host-mapped abort word
     int32_t *d_abort = nullptr;
     bool dirty = true;
@@ -461,7 +463,8 @@ slbm_status sync_table(slbm_pool *p) {
         for (size_t r = 0; r < nrow; ++r) {
             const PoolEntry &E = p->host_tab[r];
             const int64_t bytes = (int64_t)E.S * (p->q * elt + (p->q - 1) * 4) + (int64_t)E.n_links * sizeof(LinkMap);
-            if (p->groups.empty() || (p->group_bytes > 0 && acc + bytes > p->group_bytes)) {
+            if (p->groups.empty() || (p->group_bytes > 0 && acc + bytes > p->group_bytes) ||
+                (int32_t)r - p->groups.back().r0 >= PT_MAX) {
                 p->groups.push_back({(int32_t)r, (int32_t)r, {begin[0][r], begin[1][r]}, {0, 0}});
                 acc = 0;
             }
@@ -469,6 +472,26 @@ slbm_status sync_table(slbm_pool *p) {
             slbm_pool::Group &G = p->groups.back();
             G.r1 = (int32_t)r + 1;
             for (int v = 0; v < 2; ++v) G.nt[v] = begin[v][r + 1] - G.t0[v];
+        }
+    }
+    // each group's member table, for both tilings (kernel parameters)
+    p->ptab.assign(2 * p->groups.size(), PoolTable{});
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        const slbm_pool::Group &G = p->groups[gi];
+        for (int v = 0; v < 2; ++v) {
+            PoolTable &T = p->ptab[2 * gi + v];
+            T.n = G.r1 - G.r0;
+            for (int32_t r = G.r0; r < G.r1; ++r) {
+                const PoolEntry &E = p->host_tab[r];
+                const int j = r - G.r0;
+                T.first_tile[j] = begin[v][r] - G.t0[v];
+                T.pdf[j] = E.pdf;
+                T.R[j] = E.R;
+                T.S[j] = E.S;
+                T.nf[j] = E.nf;
+                T.row[j] = r;
+            }
+            T.first_tile[T.n] = G.nt[v];
         }
     }
     // the batched table is unchanged (only large members came or went): the
@@ -486,28 +509,6 @@ slbm_status sync_table(slbm_pool *p) {
                             cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_hdr, &p->host_hdr, sizeof(PoolHeader), cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess && p->ctas_per_sm == 0 && tile > 0) {
-        // tile descriptors for both tilings
-        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-            const int32_t n = begin[v][nrow];
-            p->n_tiles[v] = n;
-            if (n > p->tiles_cap[v]) {
-                if (p->d_tiles[v]) cudaFree(p->d_tiles[v]);
-                p->d_tiles[v] = nullptr;
-                e = cudaMalloc(&p->d_tiles[v], (size_t)n * sizeof(TileDesc));
-                p->tiles_cap[v] = e == cudaSuccess ? n : 0;
-            }
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(p->d_begin, begin[v].data(), nrow * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, p->stream);
-            if (e == cudaSuccess) {
-                fill_tiles<<<dim3(64, (unsigned)p->host_tab.size()), 256, 0, p->stream>>>(
-                    (const PoolEntry *)p->d_tab, (int32_t)p->host_tab.size(), cells[v], p->d_begin, p->d_tiles[v]);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);   // `begin` is reused
-        }
-    }
     // pageable source: make sure the copy has consumed the staging arrays
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pcuda(e, "pool table upload");
@@ -627,9 +628,9 @@ cudaError_t launch_one(slbm_pool *p, int32_t t, const slbm_pool::Group *g) {
         const int32_t nt = g->nt[v];
         if (nt == 0) return cudaSuccess;
         const int32_t pf = (mode == 3 || mode == 4) ? p->pf_dist : 0;
-        tk<<<(unsigned)nt, POOL_THREADS, 0, p->stream>>>(
-            (const PoolEntry *)p->d_tab, p->d_tiles[v] + g->t0[v], t, p->d_abort, (int32_t *)p->d_status, p->up,
-            nt, pf);
+        const size_t gi = (size_t)(g - p->groups.data());
+        tk<<<(unsigned)nt, POOL_THREADS, 0, p->stream>>>((const PoolEntry *)p->d_tab, p->ptab[2 * gi + v], t,
+                                                          p->d_abort, (int32_t *)p->d_status, p->up, pf);
         return cudaGetLastError();
     }
     PoolKernel kern = kernel_of(p, mode);
@@ -669,7 +670,6 @@ slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void 
     if (e == cudaSuccess) e = cudaMalloc(&p->d_hdr, sizeof(PoolHeader));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_red, (size_t)capacity * 5 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_begin, (size_t)capacity * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&p->h_abort, sizeof(int32_t), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *p->h_abort = 0;
@@ -923,9 +923,7 @@ void slbm_pool_free(slbm_pool_t *p) {
     if (p->d_hdr) cudaFree(p->d_hdr);
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_red) cudaFree(p->d_red);
-    for (int v = 0; v < 2; ++v)
-        if (p->d_tiles[v]) cudaFree(p->d_tiles[v]);
-    if (p->d_begin) cudaFree(p->d_begin);
+
     if (p->h_abort) cudaFreeHost(p->h_abort);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     cudaGetLastError();
