@@ -205,12 +205,13 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
             for (int r = 0; r < Q - 1; ++r) bulk_prefetch_l2(pt.R[mf] + r * pt.S[mf] + first, (uint32_t)cells * 4u);
         }
     }
+    // The stop word is tested only once the first loads of the tile are in
+    // flight (a halted CTA still writes nothing), so its latency overlaps them.
     int32_t halt = *(volatile int32_t *)stop;
-    if (!halt && (t & 255) == 0 && abort_flag && *abort_flag) {
+    if ((t & 255) == 0 && abort_flag && *abort_flag) {
         if (threadIdx.x == 0) atomicCAS(stop, 0, (int32_t)SLBM_EABORTED);
         halt = 1;
     }
-    if (halt) return;
     const int m = pt_member(pt, t);
     struct {
         int32_t first, member;
@@ -231,6 +232,8 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
 #pragma unroll
             for (int c = 0; c < CPT; ++c) g[c][i] = St::raw(x.v[c]);
         }
+        asm volatile("" ::: "memory");       // the loads above stay ahead of the test
+        if (halt) return;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
         const bool full = k0 + CPT <= nf;
@@ -255,6 +258,8 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
         e[0] = 0;
 #pragma unroll
         for (int i = 1; i < Q; ++i) e[i] = __ldcs(D.R + (i - 1) * S + k);
+        asm volatile("" ::: "memory");       // the loads above stay ahead of the test
+        if (halt) return;
         // members without links never take the link branch of the BC path
         odd_cell<Q, ST, BC>(pdf, e, k, S, BC ? tab[D.member].maps : nullptr, p);
     }
