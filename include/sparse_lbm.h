@@ -328,10 +328,11 @@ slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph);
 slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem);
 /* Launch variant.  ctas_per_sm == 0 (default): tile grid -- one CTA of 128
  * threads per tile of the concatenated cell lists (256-cell tiles for the even
- * step, 128-cell tiles for the odd step), from per-tile descriptors built on
- * the device when the membership changes (threads is ignored).  ctas_per_sm > 0: persistent walker
- * with `threads` cells per tile (32..128, multiple of 32) and at most
- * ctas_per_sm CTAs per SM. */
+ * step, 128-cell tiles for the odd step); each launch carries its group's
+ * member table (up to 256 members) as a kernel parameter, rebuilt on the host
+ * when the membership changes (threads is ignored).  ctas_per_sm > 0:
+ * persistent walker with `threads` cells per tile (32..128, multiple of 32)
+ * and at most ctas_per_sm CTAs per SM. */
 slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm);
 /* Members with at least split_cells fluid cells (default 524288) are stepped
  * by their own single-domain kernels inside the pool's launch sequence (and
