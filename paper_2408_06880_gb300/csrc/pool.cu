@@ -1,23 +1,24 @@
-// pool.cu -- batched stepping of many sparse domains with one persistent
-// kernel per time step (the method's AA update, Sec. 5.1, over the
-// concatenation of the member domains' compacted cell lists).
+// pool.cu -- batched stepping of many sparse domains (the method's AA update,
+// Sec. 5.1, over the concatenation of the member domains' compacted cell
+// lists).
 //
-// The pool keeps a device table of its members, sorted by their first global
-// tile: PDF-list, odd-step slot list, link maps, stride, cell count, tile
-// offset, the parity of the member at the start of the current launch
-// sequence, and the member's collision constants.  A launch splits the global
-// tiles (blockDim cells each) into one contiguous range per CTA of a
-// persistent grid; the member owning a tile decides, by its parity, between
-// the cell-local even update and the index-driven odd update.  Members at
-// different parities share a launch.
+// The pool keeps a device table of its members: PDF-list, odd-step slot
+// list, link maps, stride, cell count, tile offset, the parity of the member
+// at the start of the current launch sequence, and the member's collision
+// constants.  The member owning a tile decides, by its parity, between the
+// cell-local even update and the index-driven odd update, so members at
+// different parities can share a launch.
 //
-// Two launch variants.  Persistent walker (ctas_per_sm > 0): the grid size and
-// the table address never change, so a captured CUDA graph of K launches
-// stays valid when members join or leave; the host rewrites the table
-// (stream-ordered) instead.  Tile grid (default): one CTA per tile, from
-// per-tile descriptors; its graphs are re-captured after membership changes.  A host-mapped abort word is polled every
-// few tiles; a raised flag makes every CTA stop early and the next
-// synchronising pool call reports SLBM_EABORTED.
+// Two launch variants.  Tile grid (default): one CTA per tile of a group of
+// members, the group's member table passed as a kernel parameter; members at
+// or above a cell threshold run their own single-domain kernels in the same
+// sequence; graphs of the groups are re-captured after membership changes.
+// Persistent walker (ctas_per_sm > 0): the grid size and the table address
+// never change, so a captured CUDA graph of K launches stays valid when
+// members join or leave; the host rewrites the table (stream-ordered)
+// instead.  A host-mapped abort word is polled every few tiles; a raised flag
+// makes every CTA stop early and the next synchronising pool call reports
+// SLBM_EABORTED.
 #include <cstring>
 #include <mutex>
 #include <tuple>
@@ -144,14 +145,12 @@ __global__ void __launch_bounds__(128, 4) pool_step_kernel(const PoolHeader *__r
 
 // ---------------------------------------------------------------------------
 // Tile-grid variant (the default): one CTA per tile of the concatenated cell
-// lists.  Each tile has a 32-byte descriptor (PDF-list, slot list, stride,
-// cell count, first cell, member) built on the device when the membership
-// changes; a CTA reads it with one uniform load and starts on its cells.  Two
-// tilings: 256-cell tiles for the cell-local even step (128 threads x 2
-// consecutive cells, vector accesses) and 128-cell tiles for the odd step and
-// for launches that mix parities (128 threads x 1 cell).  Every 256th CTA
-// reads the host-mapped abort word and raises a device stop word that all
-// CTAs read before starting.
+// lists of a group of members.  Two tilings: 256-cell tiles for the
+// cell-local even step (128 threads x 2 consecutive cells, vector accesses)
+// and 128-cell tiles for the odd step and for launches that mix parities (128
+// threads x 1 cell).  Every 256th CTA reads the host-mapped abort word and
+// raises a device stop word; every CTA tests the stop word before its first
+// store.
 constexpr int POOL_THREADS = 128;
 
 // The members of one launch (a group), passed by value as a kernel parameter
