@@ -105,7 +105,7 @@ typedef struct {
  * five stress moments (the viscosity, Eq. 7) and, until
  * sparse_lbm_set_mrt_rates says otherwise, s_e = 1.19, s_eps = s_pi = 1.4,
  * s_q = 1.2, s_m = 1.98; trt_magic is ignored.  Sparse (AA) and pull
- * layouts, launch variants 0 and 2; no pools. */
+ * layouts, launch variant 0 (and 2 on the odd step); no pools. */
 
 /* SLBM_LAYOUT_SPARSE_PULL -- the two-grid pull scheme the paper compares the
  * AA pattern with (Sec. 5.1, Table 2's pull row): the same compacted cells and
@@ -232,20 +232,27 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
  *            `threads` cells (64 or 128) and keep `cells` tiles (2 or 4) of
  *            index-list rows (odd) or PDF rows (even) in flight in shared
  *            memory through asynchronous bulk copies; sparse FP32/FP16 only;
- * variant 2: odd step only, as variant 0 (1 or 2 cells per thread), plus an
+ * variant 2: even step: as variant 0 with 2 or 4 cells per thread that
+ *            collide in pairs through the paired FP32 instructions (one
+ *            instruction per two cells; the same roundings per cell); SRT/TRT.
+ *            Odd step: as variant 0 (1 or 2 cells per thread), plus an
  *            asynchronous bulk L2 prefetch of the index-list rows of the block
  *            that will run one residency wave later;
- * variant 3: as variant 2, but each thread re-reads its slots from the list
- *            before the scatter instead of keeping them in registers (domains
- *            without inlet/outlet links; others run variant 2);
+ * variant 3: even step: variant 1 (tile 64 or 128, 2 or 4 stages; sparse
+ *            FP32/FP16) with 2 cells per thread collided in pairs as in
+ *            variant 2; SRT/TRT.  Odd step: as variant 2, but each thread
+ *            re-reads its slots from the list before the scatter instead of
+ *            keeping them in registers (domains without inlet/outlet links;
+ *            others run variant 2);
  * variant 4: odd step only, as variant 2 (1 or 2 cells per thread), with the
  *            slots read as 16-bit link codes (sparse_lbm_export_codes) and
  *            the L2 prefetch of the codes: 2 instead of 4 index bytes per
  *            link.  The codes ((Q-1) x S x 2 bytes) are built and allocated
  *            on the first selection of this variant (SLBM_ENOMEM if the
  *            allocation fails).
- * Defaults: even variant 0, 64 x 2 (FP16: variant 1, 128 x 2); odd variant 2,
- * 128 x 1.  Results are bit-for-bit the same for every shape. */
+ * Defaults: even variant 2, 64 x 4 (FP16 D3Q27: variant 3, tile 128, 4
+ * stages; MRT and BF16: variant 0, 64 x 2); odd variant 2, 128 x 1.  Results
+ * are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch

@@ -119,7 +119,33 @@ __device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
     }
 }
 
-template <int Q, int ST, int CPT, int OP = OP_TRT>
+// Collision of the CPT cells a thread holds (g[c][i]: cell c, direction i).
+// PACK (TRT/SRT, CPT even): cells c and c + 1 share one pass of the
+// collision in the two lanes of the paired FP32 instructions -- the same
+// roundings per cell as the scalar pass, half the FP instructions.
+template <int Q, bool SCALED, int OP, int CPT, bool PACK>
+__device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideParams &p) {
+    if constexpr (PACK) {
+        static_assert(OP == OP_TRT && CPT % 2 == 0, "paired collision: TRT/SRT, an even number of cells");
+#pragma unroll
+        for (int c = 0; c < CPT; c += 2) {
+            F2 h[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i] = F2{make_float2(g[c][i], g[c + 1][i])};
+            collide_v<Q, SCALED>(h, p);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                g[c][i] = h[i].v.x;
+                g[c + 1][i] = h[i].v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) collide_op<Q, SCALED, OP>(g[c], p);
+    }
+}
+
+template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false>
 __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
                                                       int32_t nf, CollideParams p) {
     using St = Store<ST>;
@@ -134,8 +160,7 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
 #pragma unroll
         for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
     }
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) collide_op<Q, St::scaled, OP>(g[c], p);
+    collide_cells<Q, St::scaled, OP, CPT, PACK>(g, p);
     const bool full = k0 + CPT <= nf;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -446,8 +471,9 @@ __global__ void __launch_bounds__(TILE) aa_odd_staged_kernel(typename Store<ST>:
     __syncthreads();
 }
 
-// TILE cells per tile, CPT consecutive cells per thread (TILE / CPT threads).
-template <int Q, int ST, int TILE, int NSTAGE, int CPT = 1>
+// TILE cells per tile, CPT consecutive cells per thread (TILE / CPT threads);
+// PACK: the cells of a thread collide in pairs (collide_cells).
+template <int Q, int ST, int TILE, int NSTAGE, int CPT = 1, bool PACK = false>
 __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                                     int32_t S, int32_t nf, CollideParams p,
                                                                     int32_t *err) {
@@ -504,8 +530,7 @@ __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Sto
         }
         const int32_t k0 = t * TILE + CPT * tid;
         if (k0 < nf) {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+            collide_cells<Q, St::scaled, OP_TRT, CPT, PACK>(g, p);
             const bool full = k0 + CPT <= nf;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {

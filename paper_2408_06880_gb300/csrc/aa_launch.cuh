@@ -33,7 +33,8 @@ static unsigned persistent_grid(K kernel, int threads, int64_t tiles, size_t sme
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, slots));
 }
 
-template <int Q, int ST, int TILE, int NSTAGE>
+// PACK (even step only): 2 cells per thread, collided in pairs.
+template <int Q, int ST, int TILE, int NSTAGE, bool PACK = false>
 static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
@@ -42,14 +43,14 @@ static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const int64_t tiles = S / TILE;
     if (parity == 0) {
-        if constexpr (ST == ST_F16) {    // FP16: 2 cells per thread, paired conversions
-            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2>;
+        if constexpr (ST == ST_F16 || PACK) {    // 2 cells per thread (FP16: paired conversions)
+            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2, PACK>;
             k<<<persistent_grid(k, TILE / 2, tiles), TILE / 2, 0, st>>>(pdf, S, nf, p, err);
         } else {
             auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 1>;
             k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err);
         }
-    } else {
+    } else if constexpr (!PACK) {
         const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
         const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
         if (d.n_links > 0) {
@@ -134,6 +135,36 @@ static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Even step with the paired collision: variant 3 bulk-staged (tile `threads`
+// cells, `cells` stages; FP32/FP16), variant 2 -- and variant 3 in checked
+// mode -- the plain kernel with `cells` (2 or 4) cells per thread.
+template <int Q, int ST>
+static cudaError_t launch_even_packed(const Domain &d, const LaunchShape &sh, cudaStream_t st) {
+    if constexpr (ST != ST_BF16) {
+        if (sh.variant == 3 && !d.checked) {
+            switch (sh.threads * 10 + sh.cells) {
+                case 642: return launch_staged<Q, ST, 64, 2, true>(d, 0, st);
+                case 644: return launch_staged<Q, ST, 64, 4, true>(d, 0, st);
+                case 1282: return launch_staged<Q, ST, 128, 2, true>(d, 0, st);
+                case 1284: return launch_staged<Q, ST, 128, 4, true>(d, 0, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
+    using T = typename Store<ST>::T;
+    T *pdf = reinterpret_cast<T *>(d.pdf.p);
+    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
+    const CollideParams p = d.collide_params();
+    const unsigned span = (unsigned)(sh.threads * sh.cells);
+    const dim3 grid((unsigned)((nf + span - 1) / span));
+    switch (sh.cells) {
+        case 2: aa_even_kernel<Q, ST, 2, OP_TRT, true><<<grid, sh.threads, 0, st>>>(pdf, S, nf, p); break;
+        case 4: aa_even_kernel<Q, ST, 4, OP_TRT, true><<<grid, sh.threads, 0, st>>>(pdf, S, nf, p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int Q, int ST>
 static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
@@ -144,14 +175,16 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
         if (d.op == SLBM_MRT) return launch_mrt<ST>(d, parity, st);
     }
     const LaunchShape sh = d.shape[parity];
-    if (sh.variant >= 2 && parity == 0) return cudaErrorInvalidValue;
-    if (sh.variant == 1 && !d.checked && ST != ST_BF16) {
-        switch (sh.threads * 10 + sh.cells) {
-            case 642: return launch_staged<Q, ST, 64, 2>(d, parity, st);
-            case 644: return launch_staged<Q, ST, 64, 4>(d, parity, st);
-            case 1282: return launch_staged<Q, ST, 128, 2>(d, parity, st);
-            case 1284: return launch_staged<Q, ST, 128, 4>(d, parity, st);
-            default: return cudaErrorInvalidValue;
+    if (parity == 0 && sh.variant >= 2) return launch_even_packed<Q, ST>(d, sh, st);
+    if constexpr (ST != ST_BF16) {
+        if (sh.variant == 1 && !d.checked) {
+            switch (sh.threads * 10 + sh.cells) {
+                case 642: return launch_staged<Q, ST, 64, 2>(d, parity, st);
+                case 644: return launch_staged<Q, ST, 64, 4>(d, parity, st);
+                case 1282: return launch_staged<Q, ST, 128, 2>(d, parity, st);
+                case 1284: return launch_staged<Q, ST, 128, 4>(d, parity, st);
+                default: return cudaErrorInvalidValue;
+            }
         }
     }
     const CollideParams p = d.collide_params();

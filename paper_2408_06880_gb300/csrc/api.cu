@@ -272,7 +272,9 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (d.op == SLBM_MRT) default_mrt_rates(d);
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
-    if (d.storage == SLBM_FP16 && d.layout == SLBM_LAYOUT_SPARSE && d.op != SLBM_MRT) d.shape[0] = LaunchShape{128, 2, 1};
+    // even step: cells collided in pairs (SRT/TRT); FP16 D3Q27 from bulk-staged tiles
+    if (d.layout == SLBM_LAYOUT_SPARSE && d.op != SLBM_MRT && d.storage != SLBM_BF16)
+        d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -567,8 +569,8 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates) {
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
     if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
-    if (h->d.op == SLBM_MRT && variant != 0 && variant != 2)
-        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
+    if (h->d.op == SLBM_MRT && variant != 0 && !(variant == 2 && parity == 1))
+        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variant 0, and variant 2 on the odd step");
     if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
         return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
     if (variant == 0) {
@@ -581,16 +583,25 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variant covers sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
-    } else if (variant >= 2 && variant <= 4) {
-        if (parity != 1 || threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant != 3 && cells == 2)))
-            return err(SLBM_EINVAL, "variants 2..4 are for the odd step: threads 32..256 (multiple of 32), "
+    } else if (parity == 0 && variant == 2) {
+        if (threads < 32 || threads > 256 || threads % 32 || (cells != 2 && cells != 4))
+            return err(SLBM_EINVAL, "even variant 2 (paired collision): threads 32..256 (multiple of 32), "
+                                    "cells 2 or 4");
+    } else if (parity == 0 && variant == 3) {
+        if (h->d.layout != SLBM_LAYOUT_SPARSE || h->d.storage == SLBM_BF16)
+            return err(SLBM_EUNSUPPORTED, "the staged variants cover sparse FP32/FP16 domains");
+        if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
+            return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
+    } else if (parity == 1 && variant >= 2 && variant <= 4) {
+        if (threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant != 3 && cells == 2)))
+            return err(SLBM_EINVAL, "odd variants 2..4: threads 32..256 (multiple of 32), "
                                     "cells 1 (variants 2 and 4 also 2)");
         if (variant == 4) {
             const slbm_status st = ensure_codes(h->d);
             if (st != SLBM_OK) return st;
         }
     } else {
-        return err(SLBM_EINVAL, "variant must be 0..4");
+        return err(SLBM_EINVAL, "variant must be 0..3 (even step) or 0..4 (odd step)");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);

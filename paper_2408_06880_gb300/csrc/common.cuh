@@ -142,9 +142,76 @@ __device__ __forceinline__ void moments(const float (&g)[Q], float &drho, float 
     }
 }
 
-struct Vel {
-    float x, y, z;
+template <class V>
+struct VelT {
+    V x, y, z;
 };
+using Vel = VelT<float>;
+
+// Two cells' values in the two FP32 lanes of one register pair.  The paired
+// FP32 instructions of sm_100-class GPUs round each lane exactly as the
+// scalar instruction does (IEEE round-to-nearest, no flush), so a collision
+// evaluated on pairs gives the same bits per cell as the scalar one with
+// half the FP instructions.  The pair operations are written as PTX with an
+// explicit .rn rounding mode.  On its own that does not stop the assembler
+// from fusing a paired multiply and a following paired add (measured: it
+// does), while the scalar code is compiled without contraction.  So where
+// a product feeds one add alone, the collision below writes the fma itself
+// (the rest population's source term); the products that feed additions
+// otherwise (the velocity components in c.u) have several uses each, and
+// the paired kernels are tested bit for bit against the scalar ones.
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "add.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(r.v.x), "=f"(r.v.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(r.v.x), "=f"(r.v.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(r.v.x), "=f"(r.v.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("{\n\t.reg .b64 a, b, c, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 r, a, b, c;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(r.v.x), "=f"(r.v.y)
+        : "f"(a.v.x), "f"(a.v.y), "f"(b.v.x), "f"(b.v.y), "f"(c.v.x), "f"(c.v.y));
+    return r;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return f2_add(a, b); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return f2_sub(a, b); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return f2_mul(a, b); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2{make_float2(-a.v.x, -a.v.y)}; }
+
+// Scalar / pair forms used by the generic collision: broadcast of a per-cell
+// constant, fused multiply-add (one rounding), reciprocal 1/x (IEEE division).
+template <class V>
+__device__ __forceinline__ V bc(float s);
+template <>
+__device__ __forceinline__ float bc<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ F2 bc<F2>(float s) { return F2{make_float2(s, s)}; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return f2_fma(a, b, c); }
+__device__ __forceinline__ float vrcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ F2 vrcp(F2 x) { return F2{make_float2(1.0f / x.v.x, 1.0f / x.v.y)}; }
 
 // Collision in place (Eq. 3) on shifted populations held in stored units
 // (g * sigma; sigma = 1 for FP32).  TRT on each pair (i, inverse(i)) with
@@ -161,75 +228,85 @@ struct Vel {
 //   A = (1 - omega+)/2 s + omega+ g^eq+ + (1 - omega+/2) S+
 //   B = (1 - omega-)/2 d + omega- g^eq- + (1 - omega-/2) S-
 // and the terms that depend only on the weight class folded per cell.  Each
-// fmaf is one rounding; compiled without FMA contraction the sequence of
+// fma is one rounding; compiled without FMA contraction the sequence of
 // roundings is fixed, so every kernel gives the same bits for a cell.
-template <int Q, bool SCALED>
-__device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
+// V = float: one cell; V = F2: two cells, the same operations lane-wise.
+template <int Q, bool SCALED, class V>
+__device__ __forceinline__ VelT<V> collide_v(V (&g)[Q], const CollideParams &p) {
     constexpr int NP = (Q - 1) / 2;
-    float s[NP], d[NP];
+    V s[NP], d[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         s[m] = g[2 * m + 1] + g[2 * m + 2];
         d[m] = g[2 * m + 1] - g[2 * m + 2];
     }
-    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
+    V drho = g[0], jx = bc<V>(0.f), jy = bc<V>(0.f), jz = bc<V>(0.f);
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-        drho += s[m];
+        drho = drho + s[m];
         const int i = 2 * m + 1;
-        if (cx(i) > 0) jx += d[m];
-        if (cx(i) < 0) jx -= d[m];
-        if (cy(i) > 0) jy += d[m];
-        if (cy(i) < 0) jy -= d[m];
-        if (cz(i) > 0) jz += d[m];
-        if (cz(i) < 0) jz -= d[m];
+        if (cx(i) > 0) jx = jx + d[m];
+        if (cx(i) < 0) jx = jx - d[m];
+        if (cy(i) > 0) jy = jy + d[m];
+        if (cy(i) < 0) jy = jy - d[m];
+        if (cz(i) > 0) jz = jz + d[m];
+        if (cz(i) < 0) jz = jz - d[m];
     }
     if (SCALED) {
-        drho *= p.inv_scale;
-        jx *= p.inv_scale;
-        jy *= p.inv_scale;
-        jz *= p.inv_scale;
+        const V is = bc<V>(p.inv_scale);
+        drho = drho * is;
+        jx = jx * is;
+        jy = jy * is;
+        jz = jz * is;
     }
-    const float rho = 1.0f + drho;
-    const float ir = 1.0f / rho;
-    const float ux = fmaf(0.5f, p.fx, jx) * ir;
-    const float uy = fmaf(0.5f, p.fy, jy) * ir;
-    const float uz = fmaf(0.5f, p.fz, jz) * ir;
-    const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-    const float uF = fmaf(uz, p.fz, fmaf(uy, p.fy, ux * p.fx));
-    const float E = fmaf(-1.5f * rho, usq, drho);              // drho - 1.5 rho u.u
-    const float sr = SCALED ? p.scale * rho : rho;              // sigma rho
-    const float sE = SCALED ? p.scale * E : E;                  // sigma (drho - 1.5 rho u.u)
-    const float skF = SCALED ? p.scale * (p.kp * 3.0f * uF) : p.kp * 3.0f * uF;  // sigma kp 3 u.F
+    const V rho = bc<V>(1.0f) + drho;
+    const V ir = vrcp(rho);
+    const V ux = vfma(bc<V>(0.5f), bc<V>(p.fx), jx) * ir;
+    const V uy = vfma(bc<V>(0.5f), bc<V>(p.fy), jy) * ir;
+    const V uz = vfma(bc<V>(0.5f), bc<V>(p.fz), jz) * ir;
+    const V usq = vfma(uz, uz, vfma(uy, uy, ux * ux));
+    const V uF = vfma(uz, bc<V>(p.fz), vfma(uy, bc<V>(p.fy), ux * bc<V>(p.fx)));
+    const V E = vfma(bc<V>(-1.5f) * rho, usq, drho);            // drho - 1.5 rho u.u
+    const V sr = SCALED ? bc<V>(p.scale) * rho : rho;          // sigma rho
+    const V sE = SCALED ? bc<V>(p.scale) * E : E;              // sigma (drho - 1.5 rho u.u)
+    const V skF = SCALED ? bc<V>(p.scale) * (bc<V>(p.kp * 3.0f) * uF)
+                         : bc<V>(p.kp * 3.0f) * uF;            // sigma kp 3 u.F
     const float wp = p.omega_p, wm = p.omega_m;
     const float hp = 0.5f - 0.5f * wp, hm = 0.5f - 0.5f * wm;   // (1 - omega)/2
-    const float pE = wp * sE, pR = wp * sr, mR = wm * sr;
-    // rest population: even only
+    const V pE = bc<V>(wp) * sE, pR = bc<V>(wp) * sr, mR = bc<V>(wm) * sr;
+    // rest population: even only.  Its source term enters through one fma:
+    // the paired form would otherwise be open to a multiply-add contraction
+    // that the scalar form is compiled without, and both must round alike.
     {
         constexpr float w = wgt<Q>(0);
-        g[0] = fmaf(w, pE, fmaf(-wp, g[0], g[0])) - w * skF;
+        g[0] = vfma(bc<V>(-w), skF, vfma(bc<V>(w), pE, vfma(bc<V>(-wp), g[0], g[0])));
     }
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         const int i = 2 * m + 1;
         const float w = wgt<Q>(i);
-        float cu = 0.f;
-        if (cx(i) > 0) cu += ux;
-        if (cx(i) < 0) cu -= ux;
-        if (cy(i) > 0) cu += uy;
-        if (cy(i) < 0) cu -= uy;
-        if (cz(i) > 0) cu += uz;
-        if (cz(i) < 0) cu -= uz;
+        V cu = bc<V>(0.f);
+        if (cx(i) > 0) cu = cu + ux;
+        if (cx(i) < 0) cu = cu - ux;
+        if (cy(i) > 0) cu = cu + uy;
+        if (cy(i) < 0) cu = cu - uy;
+        if (cz(i) > 0) cu = cu + uz;
+        if (cz(i) < 0) cu = cu - uz;
         // class constants (folded by the compiler per weight class)
-        const float Ap = fmaf(w, pE, -(w * skF));               // omega+ w sE - w skF
-        const float Bp = (4.5f * w) * pR;                        // omega+ 4.5 w sigma rho
-        const float Cm = (3.0f * w) * mR;                        // omega- 3 w sigma rho
-        const float A = fmaf(hp, s[m], fmaf(Bp, cu * cu, fmaf(p.alpha[m], cu, Ap)));
-        const float B = fmaf(hm, d[m], fmaf(Cm, cu, p.kappa[m]));
+        const V Ap = vfma(bc<V>(w), pE, -(bc<V>(w) * skF));     // omega+ w sE - w skF
+        const V Bp = bc<V>(4.5f * w) * pR;                       // omega+ 4.5 w sigma rho
+        const V Cm = bc<V>(3.0f * w) * mR;                       // omega- 3 w sigma rho
+        const V A = vfma(bc<V>(hp), s[m], vfma(Bp, cu * cu, vfma(bc<V>(p.alpha[m]), cu, Ap)));
+        const V B = vfma(bc<V>(hm), d[m], vfma(Cm, cu, bc<V>(p.kappa[m])));
         g[i] = A + B;
         g[i + 1] = A - B;
     }
-    return Vel{ux, uy, uz};
+    return VelT<V>{ux, uy, uz};
+}
+
+template <int Q, bool SCALED>
+__device__ __forceinline__ Vel collide(float (&g)[Q], const CollideParams &p) {
+    return collide_v<Q, SCALED, float>(g, p);
 }
 
 // ---------------------------------------------------------------- MRT

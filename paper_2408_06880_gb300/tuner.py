@@ -20,7 +20,8 @@ import numpy as np
 
 from . import _capi as A
 
-EVEN_SHAPES = [(64, 1, 0), (64, 2, 0), (128, 2, 0), (64, 4, 0), (128, 2, 1), (128, 4, 1), (64, 2, 1)]
+EVEN_SHAPES = [(64, 1, 0), (64, 2, 0), (128, 2, 0), (64, 4, 0), (128, 2, 1), (128, 4, 1), (64, 2, 1),
+               (64, 2, 2), (128, 2, 2), (64, 4, 2), (128, 2, 3), (128, 4, 3), (64, 2, 3)]
 ODD_SHAPES = [(128, 1, 2), (64, 1, 2), (256, 1, 2), (128, 1, 3), (128, 1, 4), (64, 1, 4), (128, 1, 0),
               (128, 2, 1)]
 POOL_SHAPES = [(64, 0), (64, 8), (128, 4), (96, 4)]
@@ -61,12 +62,14 @@ def size_class(n_fluid: int) -> int:
 
 
 def _valid(info: dict, parity: int, shape) -> bool:
-    """Shapes the library accepts for this domain: no bulk-staged BF16; MRT
-    runs variants 0 and 2 with at most 2 cells per thread."""
-    if shape[2] == 1 and info["storage"] == A.BF16:
+    """Shapes the library accepts for this domain: no bulk-staged BF16 (even
+    variants 1 and 3, odd variant 1); MRT runs variant 0 (and 2 on the odd
+    step) with at most 2 cells per thread."""
+    staged = shape[2] == 1 or (parity == 0 and shape[2] == 3)
+    if staged and info["storage"] == A.BF16:
         return False
     if info["op"] == A.MRT:
-        return shape[2] in (0, 2) and shape[1] <= 2
+        return (shape[2] == 0 or (parity == 1 and shape[2] == 2)) and shape[1] <= 2
     return True
 
 

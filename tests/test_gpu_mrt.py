@@ -100,6 +100,8 @@ def test_mrt_refusals():
         with pytest.raises(P.SlbmError):
             d.set_launch(1, 128, 2, 1)
         with pytest.raises(P.SlbmError):
+            d.set_launch(0, 128, 2, 2)     # the paired collision is TRT/SRT only
+        with pytest.raises(P.SlbmError):
             d.set_mrt_rates(np.full(19, 2.5))
         with P.Pool(19, P.FP32, capacity=2) as pool:
             with pytest.raises(P.SlbmError):

@@ -185,6 +185,60 @@ def test_launch_shapes_are_bitwise_identical(shape, q, storage):
     assert np.array_equal(got, want)
 
 
+EVEN_PAIRED = [(64, 2, 2), (128, 2, 2), (256, 2, 2), (64, 4, 2), (256, 4, 2), (64, 2, 3), (64, 4, 3), (128, 2, 3),
+               (128, 4, 3)]
+
+
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16, P.BF16])
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("shape", EVEN_PAIRED)
+def test_paired_collision_is_bitwise_identical(shape, q, storage):
+    # the even step with cells collided in pairs (paired FP32 instructions)
+    # gives the scalar collision's bits; both geometries have an odd N_F, so
+    # the last pair is ragged; the D3Q27 case carries inlet/outlet links
+    g = _mixed_bc(13, (40, 33, 29)) if q == 27 else G.boolean_spheres(39, 0.5, 9)
+    assert int((g.flags == 0).sum()) % 2 == 1
+    kw = dict(q=q, op=P.TRT, force=(1e-5, 2e-6, -1e-6), storage=storage, scale_exp=20)
+    with gpu_domain(g, **kw) as ref:
+        ref.set_launch(0, 128, 1)
+        ref.step(9)
+        want, _ = ref.get_state()
+    with gpu_domain(g, **kw) as d:
+        if storage == P.BF16 and shape[2] == 3:
+            with pytest.raises(P.SlbmError):
+                d.set_launch(0, *shape)
+            return
+        d.set_launch(0, *shape)
+        d.step(9)
+        got, _ = d.get_state()
+        assert d.device_error() == 0
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("shape", [(64, 2, 2), (64, 4, 2), (64, 2, 3)])
+def test_paired_collision_srt_and_tiny_domain(shape):
+    # SRT (omega- = omega+) and a 3-cell channel: one pair plus a lone cell
+    for g, q, op in ((G.boolean_spheres(24, 0.6, 4), 19, P.SRT), (G.channel(1, 1, 3), 27, P.TRT)):
+        kw = dict(q=q, op=op, force=(3e-5, 0.0, 1e-6))
+        with gpu_domain(g, **kw) as ref:
+            ref.set_launch(0, 64, 1)
+            ref.step(11)
+            want, _ = ref.get_state()
+        with gpu_domain(g, **kw) as d:
+            d.set_launch(0, *shape)
+            d.step(11)
+            got, _ = d.get_state()
+        assert np.array_equal(got, want)
+
+
+def test_paired_even_shape_refusals():
+    g = G.boolean_spheres(16, 0.5, 2)
+    with gpu_domain(g, q=19, op=P.TRT) as d:
+        for bad in ((64, 1, 2), (64, 8, 2), (96, 2, 3), (128, 3, 3), (64, 2, 5)):
+            with pytest.raises(P.SlbmError):
+                d.set_launch(0, *bad)
+
+
 def test_graph_replay_and_checked_mode_match_plain_steps():
     g = _mixed_bc(11)
     kw = dict(q=27, op=P.TRT, force=(1e-5, 0.0, 0.0))
