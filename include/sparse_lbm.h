@@ -105,7 +105,8 @@ typedef struct {
  * five stress moments (the viscosity, Eq. 7) and, until
  * sparse_lbm_set_mrt_rates says otherwise, s_e = 1.19, s_eps = s_pi = 1.4,
  * s_q = 1.2, s_m = 1.98; trt_magic is ignored.  Sparse (AA) and pull
- * layouts, launch variant 0 (and 2 on the odd step); no pools. */
+ * layouts, launch variants 0 and 2 with at most 2 cells per thread; no
+ * pools. */
 
 /* SLBM_LAYOUT_SPARSE_PULL -- the two-grid pull scheme the paper compares the
  * AA pattern with (Sec. 5.1, Table 2's pull row): the same compacted cells and
@@ -234,8 +235,8 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
  *            memory through asynchronous bulk copies; sparse FP32/FP16 only;
  * variant 2: even step: as variant 0 with 2 or 4 cells per thread that
  *            collide in pairs through the paired FP32 instructions (one
- *            instruction per two cells; the same roundings per cell); SRT/TRT.
- *            Odd step: as variant 0 (1 or 2 cells per thread), plus an
+ *            instruction per two cells; the same roundings per cell); MRT:
+ *            2 cells.  Odd step: as variant 0 (1 or 2 cells per thread), plus an
  *            asynchronous bulk L2 prefetch of the index-list rows of the block
  *            that will run one residency wave later;
  * variant 3: even step: variant 1 (tile 64 or 128, 2 or 4 stages; sparse
@@ -251,8 +252,9 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
  *            on the first selection of this variant (SLBM_ENOMEM if the
  *            allocation fails).
  * Defaults: even variant 2, 64 x 4 (FP16 D3Q27: variant 3, tile 128, 4
- * stages; MRT and BF16: variant 0, 64 x 2); odd variant 2, 128 x 1.  Results
- * are bit-for-bit the same for every shape. */
+ * stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and BF16: variant 0,
+ * 64 x 2); odd variant 2, 128 x 1.  Results are bit-for-bit the same for
+ * every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch

@@ -120,19 +120,24 @@ __device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
 }
 
 // Collision of the CPT cells a thread holds (g[c][i]: cell c, direction i).
-// PACK (TRT/SRT, CPT even): cells c and c + 1 share one pass of the
+// PACK (CPT even): cells c and c + 1 share one pass of the
 // collision in the two lanes of the paired FP32 instructions -- the same
 // roundings per cell as the scalar pass, half the FP instructions.
 template <int Q, bool SCALED, int OP, int CPT, bool PACK>
 __device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideParams &p) {
     if constexpr (PACK) {
-        static_assert(OP == OP_TRT && CPT % 2 == 0, "paired collision: TRT/SRT, an even number of cells");
+        static_assert(CPT % 2 == 0, "paired collision: an even number of cells");
 #pragma unroll
         for (int c = 0; c < CPT; c += 2) {
             F2 h[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i] = F2{make_float2(g[c][i], g[c + 1][i])};
-            collide_v<Q, SCALED>(h, p);
+            if constexpr (OP == OP_MRT) {
+                static_assert(Q == 19, "MRT is defined for D3Q19");
+                collide_mrt_v<SCALED>(h, p);
+            } else {
+                collide_v<Q, SCALED>(h, p);
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 g[c][i] = h[i].v.x;

@@ -98,7 +98,8 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
     return e;
 }
 
-// MRT domains (D3Q19): the plain even kernel (1 or 2 cells per thread) and
+// MRT domains (D3Q19): the plain even kernel (1 or 2 cells per thread; variant
+// 2: the 2 cells collided in pairs) and
 // the odd kernel (1 or 2 cells, L2 index prefetch unless variant 0; checked
 // mode), with the MRT collision.
 template <int ST>
@@ -111,6 +112,7 @@ static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
         if (sh.cells == 1) aa_even_kernel<19, ST, 1, OP_MRT><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p);
+        else if (sh.variant == 2) aa_even_kernel<19, ST, 2, OP_MRT, true><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
         else aa_even_kernel<19, ST, 2, OP_MRT><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
         return cudaGetLastError();
     }

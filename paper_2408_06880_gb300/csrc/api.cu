@@ -272,9 +272,14 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (d.op == SLBM_MRT) default_mrt_rates(d);
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
-    // even step: cells collided in pairs (SRT/TRT); FP16 D3Q27 from bulk-staged tiles
-    if (d.layout == SLBM_LAYOUT_SPARSE && d.op != SLBM_MRT && d.storage != SLBM_BF16)
-        d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
+    // even step: cells collided in pairs (measured faster except for FP16 MRT
+    // and untimed BF16); FP16 D3Q27 from bulk-staged tiles
+    if (d.layout == SLBM_LAYOUT_SPARSE && d.storage != SLBM_BF16) {
+        if (d.op != SLBM_MRT)
+            d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
+        else if (d.storage == SLBM_FP32)
+            d.shape[0] = LaunchShape{64, 2, 2};
+    }
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -569,8 +574,8 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates) {
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
     if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
-    if (h->d.op == SLBM_MRT && variant != 0 && !(variant == 2 && parity == 1))
-        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variant 0, and variant 2 on the odd step");
+    if (h->d.op == SLBM_MRT && variant != 0 && variant != 2)
+        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
     if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
         return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
     if (variant == 0) {

@@ -363,118 +363,126 @@ __host__ __device__ constexpr bool mrt_odd_row(int a) {
 // transforms run on the sums and differences of the 9 inverse pairs: an even
 // row sees g_0 and the pair sums, an odd row the pair differences, and the
 // back transform yields both members of a pair from one even and one odd sum.
-template <bool SCALED>
-__device__ __forceinline__ Vel collide_mrt(float (&g)[19], const CollideParams &p) {
+template <bool SCALED, class V>
+__device__ __forceinline__ VelT<V> collide_mrt_v(V (&g)[19], const CollideParams &p) {
     constexpr int NP = 9;
-    float sg[NP], dg[NP];
+    V sg[NP], dg[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         sg[m] = g[2 * m + 1] + g[2 * m + 2];
         dg[m] = g[2 * m + 1] - g[2 * m + 2];
     }
-    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
+    V drho = g[0], jx = bc<V>(0.f), jy = bc<V>(0.f), jz = bc<V>(0.f);
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
-        drho += sg[m];
+        drho = drho + sg[m];
         const int i = 2 * m + 1;
-        if (cx(i) > 0) jx += dg[m];
-        if (cx(i) < 0) jx -= dg[m];
-        if (cy(i) > 0) jy += dg[m];
-        if (cy(i) < 0) jy -= dg[m];
-        if (cz(i) > 0) jz += dg[m];
-        if (cz(i) < 0) jz -= dg[m];
+        if (cx(i) > 0) jx = jx + dg[m];
+        if (cx(i) < 0) jx = jx - dg[m];
+        if (cy(i) > 0) jy = jy + dg[m];
+        if (cy(i) < 0) jy = jy - dg[m];
+        if (cz(i) > 0) jz = jz + dg[m];
+        if (cz(i) < 0) jz = jz - dg[m];
     }
     if (SCALED) {
-        drho *= p.inv_scale;
-        jx *= p.inv_scale;
-        jy *= p.inv_scale;
-        jz *= p.inv_scale;
+        const V is = bc<V>(p.inv_scale);
+        drho = drho * is;
+        jx = jx * is;
+        jy = jy * is;
+        jz = jz * is;
     }
-    const float rho = 1.0f + drho;
-    const float ir = 1.0f / rho;
-    const float ux = fmaf(0.5f, p.fx, jx) * ir;
-    const float uy = fmaf(0.5f, p.fy, jy) * ir;
-    const float uz = fmaf(0.5f, p.fz, jz) * ir;
-    const float usq = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-    const float uF = fmaf(uz, p.fz, fmaf(uy, p.fy, ux * p.fx));
+    const V rho = bc<V>(1.0f) + drho;
+    const V ir = vrcp(rho);
+    const V ux = vfma(bc<V>(0.5f), bc<V>(p.fx), jx) * ir;
+    const V uy = vfma(bc<V>(0.5f), bc<V>(p.fy), jy) * ir;
+    const V uz = vfma(bc<V>(0.5f), bc<V>(p.fz), jz) * ir;
+    const V usq = vfma(uz, uz, vfma(uy, uy, ux * ux));
+    const V uF = vfma(uz, bc<V>(p.fz), vfma(uy, bc<V>(p.fy), ux * bc<V>(p.fx)));
     const float sig = SCALED ? p.scale : 1.0f;
     // non-equilibrium and source, as pair sums (even) and differences (odd):
     //   geq_i +- geq_ib = 2 w (drho + rho (4.5 cu^2 - 1.5 u.u)),  2 w 3 rho cu
     //   S_i +- S_ib     = 2 w (9 cu cF - 3 u.F),                   2 w 3 cF
-    const float e0 = fmaf(-1.5f * rho, usq, drho);               // drho - 1.5 rho u.u
-    const float x0 = fmaf(-sig * wgt<19>(0), e0, g[0]);
-    const float s0 = -3.0f * sig * wgt<19>(0) * uF;
-    float xs[NP], xd[NP], ss[NP], sd[NP];
+    const V e0 = vfma(bc<V>(-1.5f) * rho, usq, drho);           // drho - 1.5 rho u.u
+    const V x0 = vfma(bc<V>(-sig * wgt<19>(0)), e0, g[0]);
+    const V s0 = bc<V>(-3.0f * sig * wgt<19>(0)) * uF;
+    V xs[NP], xd[NP], ss[NP];
+    float sd[NP];                                                // per-cell constant
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         const int i = 2 * m + 1;
         const float w2 = 2.0f * wgt<19>(i) * sig;
-        float cu = 0.f, cF = 0.f;
-        if (cx(i) > 0) { cu += ux; cF += p.fx; }
-        if (cx(i) < 0) { cu -= ux; cF -= p.fx; }
-        if (cy(i) > 0) { cu += uy; cF += p.fy; }
-        if (cy(i) < 0) { cu -= uy; cF -= p.fy; }
-        if (cz(i) > 0) { cu += uz; cF += p.fz; }
-        if (cz(i) < 0) { cu -= uz; cF -= p.fz; }
-        xs[m] = fmaf(-w2, fmaf(4.5f * rho * cu, cu, e0), sg[m]);
-        xd[m] = fmaf(-w2, 3.0f * rho * cu, dg[m]);
-        ss[m] = w2 * fmaf(9.0f * cu, cF, -3.0f * uF);
+        V cu = bc<V>(0.f);
+        float cF = 0.f;
+        if (cx(i) > 0) { cu = cu + ux; cF += p.fx; }
+        if (cx(i) < 0) { cu = cu - ux; cF -= p.fx; }
+        if (cy(i) > 0) { cu = cu + uy; cF += p.fy; }
+        if (cy(i) < 0) { cu = cu - uy; cF -= p.fy; }
+        if (cz(i) > 0) { cu = cu + uz; cF += p.fz; }
+        if (cz(i) < 0) { cu = cu - uz; cF -= p.fz; }
+        xs[m] = vfma(bc<V>(-w2), vfma(bc<V>(4.5f) * rho * cu, cu, e0), sg[m]);
+        xd[m] = vfma(bc<V>(-w2), bc<V>(3.0f) * rho * cu, dg[m]);
+        ss[m] = bc<V>(w2) * vfma(bc<V>(9.0f) * cu, bc<V>(cF), bc<V>(-3.0f) * uF);
         sd[m] = w2 * 3.0f * cF;
     }
-    float dm[19];
+    V dm[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
-        dm[a] = 0.f;
+        dm[a] = bc<V>(0.f);
         if (a == 0 || a == 3 || a == 5 || a == 7) continue;       // conserved
-        float mx = 0.f, ms = 0.f;
+        V mx = bc<V>(0.f), ms = bc<V>(0.f);
         if (!mrt_odd_row(a)) {
-            mx = (float)mrt_m(a, 0) * x0;
-            ms = (float)mrt_m(a, 0) * s0;
+            mx = bc<V>((float)mrt_m(a, 0)) * x0;
+            ms = bc<V>((float)mrt_m(a, 0)) * s0;
         }
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             const int i = 2 * m + 1;
             if (mrt_m(a, i) == 0) continue;
             if (mrt_odd_row(a)) {
-                mx = fmaf((float)mrt_m(a, i), xd[m], mx);
-                ms = fmaf((float)mrt_m(a, i), sd[m], ms);
+                mx = vfma(bc<V>((float)mrt_m(a, i)), xd[m], mx);
+                ms = vfma(bc<V>((float)mrt_m(a, i)), bc<V>(sd[m]), ms);
             } else {
-                mx = fmaf((float)mrt_m(a, i), xs[m], mx);
-                ms = fmaf((float)mrt_m(a, i), ss[m], ms);
+                mx = vfma(bc<V>((float)mrt_m(a, i)), xs[m], mx);
+                ms = vfma(bc<V>((float)mrt_m(a, i)), ss[m], ms);
             }
         }
         const float sa = p.mrt[a];
-        dm[a] = fmaf(-sa, mx, (1.0f - 0.5f * sa) * ms) * (1.0f / (float)mrt_norm(a));
+        dm[a] = vfma(bc<V>(-sa), mx, bc<V>(1.0f - 0.5f * sa) * ms) * bc<V>(1.0f / (float)mrt_norm(a));
     }
     {
-        float v = g[0];
+        V v = g[0];
 #pragma unroll
         for (int a = 0; a < 19; ++a)
-            if (!mrt_odd_row(a) && a != 0 && mrt_m(a, 0) != 0) v = fmaf((float)mrt_m(a, 0), dm[a], v);
+            if (!mrt_odd_row(a) && a != 0 && mrt_m(a, 0) != 0) v = vfma(bc<V>((float)mrt_m(a, 0)), dm[a], v);
         g[0] = v;
     }
     const float kx = sig * p.fx * 0.1f, ky = sig * p.fy * 0.1f, kz = sig * p.fz * 0.1f;
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         const int i = 2 * m + 1;
-        float E = 0.f, O = 0.f;
-        if (cx(i) > 0) O += kx;
-        if (cx(i) < 0) O -= kx;
-        if (cy(i) > 0) O += ky;
-        if (cy(i) < 0) O -= ky;
-        if (cz(i) > 0) O += kz;
-        if (cz(i) < 0) O -= kz;
+        V E = bc<V>(0.f), O = bc<V>(0.f);
+        if (cx(i) > 0) O = O + bc<V>(kx);
+        if (cx(i) < 0) O = O - bc<V>(kx);
+        if (cy(i) > 0) O = O + bc<V>(ky);
+        if (cy(i) < 0) O = O - bc<V>(ky);
+        if (cz(i) > 0) O = O + bc<V>(kz);
+        if (cz(i) < 0) O = O - bc<V>(kz);
 #pragma unroll
         for (int a = 0; a < 19; ++a) {
             if (a == 0 || a == 3 || a == 5 || a == 7 || mrt_m(a, i) == 0) continue;
-            if (mrt_odd_row(a)) O = fmaf((float)mrt_m(a, i), dm[a], O);
-            else E = fmaf((float)mrt_m(a, i), dm[a], E);
+            if (mrt_odd_row(a)) O = vfma(bc<V>((float)mrt_m(a, i)), dm[a], O);
+            else E = vfma(bc<V>((float)mrt_m(a, i)), dm[a], E);
         }
-        const float gi = g[i], gb = g[i + 1];
+        const V gi = g[i], gb = g[i + 1];
         g[i] = gi + E + O;
         g[i + 1] = gb + E - O;
     }
-    return Vel{ux, uy, uz};
+    return VelT<V>{ux, uy, uz};
+}
+
+template <bool SCALED>
+__device__ __forceinline__ Vel collide_mrt(float (&g)[19], const CollideParams &p) {
+    return collide_mrt_v<SCALED, float>(g, p);
 }
 
 enum { OP_TRT = 0, OP_MRT = 1 };

@@ -178,7 +178,7 @@ __device__ __forceinline__ int pt_member(const PoolTable &T, int32_t t) {
 
 // PARITY: 0 / 1 uniform, -1 mixed (per member, from its table row).
 // UNI: uniform collision constants in `up`.  BC: handle inlet/outlet links.
-// CPT: cells per thread (2 only for the uniform even step).
+// CPT: cells per thread (2 only for the uniform even step, collided in pairs).
 // pf_dist > 0 (odd step): thread 0 also asks the bulk-copy engine to
 // prefetch into L2 the slot-list rows of the tile pf_dist ahead (about one
 // residency wave later).
@@ -233,8 +233,7 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
         }
         asm volatile("" ::: "memory");       // the loads above stay ahead of the test
         if (halt) return;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) collide<Q, St::scaled>(g[c], p);
+        collide_cells<Q, St::scaled, OP_TRT, CPT, CPT % 2 == 0>(g, p);   // pairs when CPT = 2
         const bool full = k0 + CPT <= nf;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {

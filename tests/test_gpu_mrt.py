@@ -78,7 +78,8 @@ def test_mrt_shapes_and_pull_layout_are_bitwise_identical(storage):
         ref.step(7)
         want = ref.macroscopic(P.ORDER_CELLS)
         state, _ = ref.get_state()
-    for even, odd in (((128, 1, 0), (128, 1, 0)), ((64, 2, 0), (256, 2, 2)), ((256, 1, 0), (64, 1, 2))):
+    for even, odd in (((128, 1, 0), (128, 1, 0)), ((64, 2, 0), (256, 2, 2)), ((256, 1, 0), (64, 1, 2)),
+                      ((64, 2, 2), (128, 1, 2)), ((256, 2, 2), (128, 2, 0))):
         with gpu_domain(g, **kw) as d:
             d.set_launch(0, *even)
             d.set_launch(1, *odd)
@@ -88,6 +89,26 @@ def test_mrt_shapes_and_pull_layout_are_bitwise_identical(storage):
         d.step(7)
         got = d.macroscopic(P.ORDER_CELLS)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_mrt_paired_collision_on_a_random_state():
+    # one even step from random populations: the paired MRT collision gives
+    # the scalar one's bits
+    g = G.boolean_spheres(39, 0.5, 9)
+    kw = dict(q=19, op=P.MRT, force=(1e-5, 2e-6, -1e-6))
+    rng = np.random.default_rng(5)
+    with gpu_domain(g, **kw) as ref:
+        S = ref.info["stride"]
+        x = (rng.standard_normal(19 * S) * 1e-2).astype(np.float32).view(np.uint8)
+        ref.set_state(x, 0)
+        ref.set_launch(0, 64, 1)
+        ref.step(1)
+        want, _ = ref.get_state()
+    with gpu_domain(g, **kw) as d:
+        d.set_state(x, 0)
+        d.set_launch(0, 64, 2, 2)
+        d.step(1)
+        assert np.array_equal(d.get_state()[0], want)
 
 
 def test_mrt_refusals():
@@ -100,7 +121,9 @@ def test_mrt_refusals():
         with pytest.raises(P.SlbmError):
             d.set_launch(1, 128, 2, 1)
         with pytest.raises(P.SlbmError):
-            d.set_launch(0, 128, 2, 2)     # the paired collision is TRT/SRT only
+            d.set_launch(0, 128, 4, 2)     # MRT pairs: 2 cells per thread
+        with pytest.raises(P.SlbmError):
+            d.set_launch(0, 128, 2, 3)     # no staged MRT kernel
         with pytest.raises(P.SlbmError):
             d.set_mrt_rates(np.full(19, 2.5))
         with P.Pool(19, P.FP32, capacity=2) as pool:

@@ -231,6 +231,28 @@ def test_paired_collision_srt_and_tiny_domain(shape):
         assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("q", [19, 27])
+def test_paired_collision_on_a_random_state(q):
+    # far from equilibrium every rounding of the collision shows: one even
+    # step from random populations, paired shapes against the scalar kernel
+    g = G.boolean_spheres(39, 0.5, 9)
+    kw = dict(q=q, op=P.TRT, force=(1e-5, 2e-6, -1e-6))
+    rng = np.random.default_rng(q)
+    with gpu_domain(g, **kw) as ref:
+        S = ref.info["stride"]
+        x = (rng.standard_normal(q * S) * 1e-2).astype(np.float32).view(np.uint8)
+        ref.set_state(x, 0)
+        ref.set_launch(0, 64, 1)
+        ref.step(1)
+        want, _ = ref.get_state()
+    for shape in ((64, 2, 2), (64, 4, 2), (128, 4, 3)):
+        with gpu_domain(g, **kw) as d:
+            d.set_state(x, 0)
+            d.set_launch(0, *shape)
+            d.step(1)
+            assert np.array_equal(d.get_state()[0], want), shape
+
+
 def test_paired_even_shape_refusals():
     g = G.boolean_spheres(16, 0.5, 2)
     with gpu_domain(g, q=19, op=P.TRT) as d:
