@@ -250,7 +250,10 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
  *            the L2 prefetch of the codes: 2 instead of 4 index bytes per
  *            link.  The codes ((Q-1) x S x 2 bytes) are built and allocated
  *            on the first selection of this variant (SLBM_ENOMEM if the
- *            allocation fails).
+ *            allocation fails);
+ * variant 5: odd step only, as variant 2 with 1 cell per thread, the kernel
+ *            held to 64 registers a thread (more resident warps, some
+ *            registers spilled to L1).
  * Defaults: even variant 2, 64 x 4 (FP16 D3Q27: variant 3, tile 128, 4
  * stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and BF16: variant 0,
  * 64 x 2); odd variant 2, 128 x 1.  Results are bit-for-bit the same for

@@ -200,9 +200,11 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // CODE: the slots come from the 16-bit link codes and their per-tile column
 // bases (2 bytes per link instead of 4); an escape code reads the slot from
 // the int32 list.  The decoded slot equals R(i, k) exactly.
+// MINB: resident 256-thread blocks the register allocation must allow (4:
+// at most 64 registers a thread, so more warps keep gathers in flight).
 template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false,
-          int OP = OP_TRT>
-__global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
+          int OP = OP_TRT, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                      const int32_t *__restrict__ P, int32_t S, int32_t nf,
                                                      const LinkMap *__restrict__ maps, int32_t n_links,
                                                      CollideParams p, int32_t *err, int32_t pf_dist,

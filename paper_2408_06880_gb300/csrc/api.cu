@@ -597,16 +597,16 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variants cover sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
-    } else if (parity == 1 && variant >= 2 && variant <= 4) {
-        if (threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !(variant != 3 && cells == 2)))
-            return err(SLBM_EINVAL, "odd variants 2..4: threads 32..256 (multiple of 32), "
+    } else if (parity == 1 && variant >= 2 && variant <= 5) {
+        if (threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !((variant == 2 || variant == 4) && cells == 2)))
+            return err(SLBM_EINVAL, "odd variants 2..5: threads 32..256 (multiple of 32), "
                                     "cells 1 (variants 2 and 4 also 2)");
         if (variant == 4) {
             const slbm_status st = ensure_codes(h->d);
             if (st != SLBM_OK) return st;
         }
     } else {
-        return err(SLBM_EINVAL, "variant must be 0..3 (even step) or 0..4 (odd step)");
+        return err(SLBM_EINVAL, "variant must be 0..3 (even step) or 0..5 (odd step)");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);

@@ -158,7 +158,7 @@ def test_reductions_match_fields_and_are_deterministic():
 
 SHAPES = [(64, 1, 0), (128, 1, 0), (256, 1, 0), (64, 2, 0), (256, 2, 0), (128, 4, 0), (256, 4, 0),
           (64, 2, 1), (64, 4, 1), (128, 2, 1), (128, 4, 1), (64, 1, 2), (128, 1, 2), (128, 1, 3), (64, 1, 3), (128, 2, 2),
-          (128, 1, 4), (64, 1, 4), (128, 2, 4), (256, 2, 4)]
+          (128, 1, 4), (64, 1, 4), (128, 2, 4), (256, 2, 4), (128, 1, 5), (256, 1, 5), (64, 1, 5)]
 
 
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
