@@ -237,7 +237,7 @@ def run_ours(a, rank, world):
     n_launch = len(doms) * a.lbm_steps * a.steps
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_for(kname, doms),
+                "traffic": traffic_for(traffic_key(a.storage, kname), doms),
                 "algorithmic_bytes_per_launch": round(tot[dom_par][0] / (n_launch / 2)),
                 "both_kernels": {"even_gbs": round(tot[0][0] / tot[0][1] / 1e6, 1),
                                  "odd_gbs": round(tot[1][0] / tot[1][1] / 1e6, 1),
@@ -275,16 +275,22 @@ def apply_shapes(d, a):
             d.set_launch(parity, t, c, v)
 
 
+def traffic_key(storage, kname):
+    """Name of a kernel's record in the traffic file for a PDF storage (None: no record)."""
+    prefix = {"fp32": "", "fp16": "fp16_"}.get(storage)
+    return None if prefix is None else prefix + kname
+
+
 def traffic_for(kname, doms):
     """DRAM bytes per launch from the committed ncu summary, scaled by cells,
-    or None when the kernel source changed since the capture."""
+    or None when the kernel source changed since the capture or there is no record."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_digest") != kernel_digest():
+    if kname is None or t.get("source_digest") != kernel_digest():
         return None
     per_cell = t.get("kernels", {}).get(kname, {}).get("dram_bytes_per_cell")
     if per_cell is None:

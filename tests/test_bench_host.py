@@ -89,6 +89,29 @@ def test_current_traffic_record_scales_by_mean_cells(monkeypatch, tmp_path):
     assert bench.traffic_for("aa_even", doms) is None
 
 
+def test_traffic_record_follows_the_storage(monkeypatch, tmp_path):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(
+        '{"source_digest": "d1", "kernels": {"aa_odd_kernel": {"dram_bytes_per_cell": 200.0},'
+        ' "fp16_aa_odd_kernel": {"dram_bytes_per_cell": 130.0}}}')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_digest", lambda: "d1")
+    doms = [(0.5, None, _Dom(1000))]
+    assert bench.traffic_for(bench.traffic_key("fp32", "aa_odd_kernel"), doms) == 200000
+    assert bench.traffic_for(bench.traffic_key("fp16", "aa_odd_kernel"), doms) == 130000
+    assert bench.traffic_key("bf16", "aa_odd_kernel") is None
+    assert bench.traffic_for(bench.traffic_key("bf16", "aa_odd_kernel"), doms) is None
+
+
+def test_committed_traffic_record_names_the_benchmarked_kernels():
+    import json
+    with open(bench.os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)
+    for storage in ("fp32", "fp16"):
+        for k in ("aa_even_kernel", "aa_odd_kernel"):
+            assert bench.traffic_key(storage, k) in rec["kernels"]
+
+
 def test_odd_lbm_step_count_is_refused(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--lbm-steps", "7"])
     with pytest.raises(SystemExit):
