@@ -200,16 +200,12 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // CODE: the slots come from the 16-bit link codes and their per-tile column
 // bases (2 bytes per link instead of 4); an escape code reads the slot from
 // the int32 list.  The decoded slot equals R(i, k) exactly.
-// MINB: resident 256-thread blocks the register allocation must allow (4:
-// at most 64 registers a thread, so more warps keep gathers in flight).
-template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false,
-          int OP = OP_TRT, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
-                                                     const int32_t *__restrict__ P, int32_t S, int32_t nf,
-                                                     const LinkMap *__restrict__ maps, int32_t n_links,
-                                                     CollideParams p, int32_t *err, int32_t pf_dist,
-                                                     const uint16_t *__restrict__ code = nullptr,
-                                                     const int32_t *__restrict__ cbase = nullptr) {
+template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD, bool CODE, int OP>
+__device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ pdf, const int32_t *__restrict__ P,
+                                            int32_t S, int32_t nf, const LinkMap *__restrict__ maps,
+                                            int32_t n_links, const CollideParams &p, int32_t *err,
+                                            int32_t pf_dist, const uint16_t *__restrict__ code,
+                                            const int32_t *__restrict__ cbase) {
     using St = Store<ST>;
     using T = typename St::T;
     const int32_t span = blockDim.x * CPT;
@@ -320,6 +316,30 @@ __global__ void __launch_bounds__(256, MINB) aa_odd_kernel(typename Store<ST>::T
             pdf[R[c][i]] = St::pack(v);
         }
     }
+}
+
+template <int Q, int ST, int CPT, bool HAS_BC, bool CHECK, bool RELOAD = false, bool CODE = false,
+          int OP = OP_TRT>
+__global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__restrict__ pdf,
+                                                     const int32_t *__restrict__ P, int32_t S, int32_t nf,
+                                                     const LinkMap *__restrict__ maps, int32_t n_links,
+                                                     CollideParams p, int32_t *err, int32_t pf_dist,
+                                                     const uint16_t *__restrict__ code = nullptr,
+                                                     const int32_t *__restrict__ cbase = nullptr) {
+    aa_odd_body<Q, ST, CPT, HAS_BC, CHECK, RELOAD, CODE, OP>(pdf, P, S, nf, maps, n_links, p, err, pf_dist, code,
+                                                              cbase);
+}
+
+// The plain odd kernel (1 cell per thread, L2 index prefetch) held to 64
+// registers a thread -- four resident 256-thread blocks -- so that more warps
+// keep gathers in flight, at the cost of some registers spilled to L1.
+template <int Q, int ST, bool HAS_BC>
+__global__ void __launch_bounds__(256, 4) aa_odd_kernel_r64(typename Store<ST>::T *__restrict__ pdf,
+                                                            const int32_t *__restrict__ P, int32_t S, int32_t nf,
+                                                            const LinkMap *__restrict__ maps, int32_t n_links,
+                                                            CollideParams p, int32_t *err, int32_t pf_dist) {
+    aa_odd_body<Q, ST, 1, HAS_BC, false, false, false, OP_TRT>(pdf, P, S, nf, maps, n_links, p, err, pf_dist,
+                                                                nullptr, nullptr);
 }
 
 

@@ -223,10 +223,9 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
     }
     // variant 5: variant 2 held to 64 registers a thread (more resident warps)
     if (sh.variant == 5) {
-        auto kb = bc ? aa_odd_kernel<Q, ST, 1, true, false, false, false, OP_TRT, 4>
-                     : aa_odd_kernel<Q, ST, 1, false, false, false, false, OP_TRT, 4>;
+        auto kb = bc ? aa_odd_kernel_r64<Q, ST, true> : aa_odd_kernel_r64<Q, ST, false>;
         const int32_t pfb = (int32_t)persistent_grid(kb, sh.threads, INT32_MAX);
-        kb<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfb, nullptr, nullptr);
+        kb<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfb);
         return cudaGetLastError();
     }
     // variant 3: slots re-read before the scatter (no links), with the L2 prefetch
