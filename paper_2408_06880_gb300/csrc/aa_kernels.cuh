@@ -304,16 +304,16 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
         const int32_t k = kb + c * blockDim.x;
         if (!valid[c]) continue;
         pdf[k] = St::pack(g[c][0]);
-        if (RELOAD) {
+        if constexpr (RELOAD) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) pdf[__ldcs(P + (i - 1) * S + k)] = St::pack(g[c][inv(i)]);
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            float v = g[c][inv(i)];
-            if (HAS_BC && e[c][i] < 0) v = apply_link(maps[-(e[c][i] + 1)], v, u[c].x, u[c].y, u[c].z, p.scale);
-            pdf[R[c][i]] = St::pack(v);
+            for (int i = 1; i < Q; ++i) {
+                float v = g[c][inv(i)];
+                if (HAS_BC && e[c][i] < 0) v = apply_link(maps[-(e[c][i] + 1)], v, u[c].x, u[c].y, u[c].z, p.scale);
+                pdf[R[c][i]] = St::pack(v);
+            }
         }
     }
 }
