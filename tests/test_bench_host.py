@@ -119,3 +119,16 @@ def test_odd_lbm_step_count_is_refused(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--porosities", "0.3,0.9"])
     a = bench.parse()
     assert a.porosities == (0.3, 0.9) and a.gpus == 1 and a.warmup >= 3
+
+
+def test_reference_arm_samples_every_domain_of_the_workload(monkeypatch):
+    # a tiny sweep: the reference line carries our arm's workload and metric,
+    # and its steps cycle through every porosity of the sweep
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--size", "16", "--porosities", "0.5,0.7",
+                                      "--steps", "2", "--warmup", "1"])
+    a = bench.parse()
+    out = bench.run_reference(a)
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
+    assert out["config"]["workload"] == bench.workload_name(a)
+    assert "0.5/0.7" in out["config"]["sample"] and out["value"] > 0
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
