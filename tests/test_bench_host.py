@@ -132,3 +132,11 @@ def test_reference_arm_samples_every_domain_of_the_workload(monkeypatch):
     assert out["config"]["workload"] == bench.workload_name(a)
     assert "0.5/0.7" in out["config"]["sample"] and out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baseline_covers_every_domain(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--size", "16", "--porosities", "0.5,0.7", "--cpu-seconds", "0"])
+    a = bench.parse()
+    out = bench.cpu_baseline(a)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] >= 1
+    assert "4 LBM steps" in out["sample"] and "0.5/0.7" in out["sample"]     # one 2-step run per domain
