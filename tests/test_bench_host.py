@@ -130,7 +130,8 @@ def test_reference_arm_samples_every_domain_of_the_workload(monkeypatch):
     out = bench.run_reference(a)
     assert out["impl"] == "reference" and out["metric"] == bench.METRIC and out["unit"] == bench.UNIT
     assert out["config"]["workload"] == bench.workload_name(a)
-    assert "0.5/0.7" in out["config"]["sample"] and out["value"] > 0
+    assert "blocks of 1/1" in out["config"]["sample"] and "0.5/0.7" in out["config"]["sample"]
+    assert out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
 
 
