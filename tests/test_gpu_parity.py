@@ -8,7 +8,7 @@ import pytest
 
 import geometry as G
 import oracle as O
-from helpers import gpu_domain, gpu_fields, oracle_fields, oracle_problem, rel_l2, fluid_mask
+from helpers import gpu_domain, gpu_fields, oracle_fields, rel_l2, fluid_mask
 
 pytestmark = pytest.mark.gpu
 

@@ -7,7 +7,6 @@ Poiseuille profile at the TRT magic combination."""
 import math
 
 import numpy as np
-import pytest
 
 import geometry as G
 import oracle as O
