@@ -155,11 +155,16 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
 /* Advance n >= 0 time steps (Eqs. 3-4 fused, AA pattern of Sec. 5.1): step t
  * even -> cell-local collide writing each post-collision PDF into the inverse
  * direction's slot; t odd -> read the index-list, gather through it, collide,
- * scatter back to the slots read.  Asynchronous on the handle's stream. */
+ * scatter back to the slots read.  Asynchronous on the handle's stream.
+ * Errors: SLBM_EINVAL (null handle or n < 0), SLBM_ECUDA (a launch failed;
+ * the step counter stops at the last step launched).  Faults found by the
+ * kernels (checked mode, staging timeouts) are latched on the device and
+ * reported by sparse_lbm_device_error. */
 slbm_status sparse_lbm_step(slbm_t *h, int32_t n);
 
 /* Same as sparse_lbm_step but replays a CUDA graph holding n launches
- * (captured on first use for each (n, parity) and cached). */
+ * (captured on first use for each (n, parity) and cached).  Errors as
+ * sparse_lbm_step; a failed capture or replay is SLBM_ECUDA. */
 slbm_status sparse_lbm_step_graph(slbm_t *h, int32_t n);
 
 /* Macroscopic fields (Eq. 1 with the Guo half-force velocity) of the current
@@ -183,6 +188,8 @@ slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem);
 slbm_status sparse_lbm_init_equilibrium(slbm_t *h, const float *rho, const float *u,
                                         int32_t order, int32_t mem);
 
+/* Sizes and state of a domain (the fields of slbm_info) into caller memory.
+ * Synchronous, no device access.  Errors: SLBM_EINVAL for a null argument. */
 slbm_status sparse_lbm_info(const slbm_t *h, slbm_info *out);
 
 /* Copy the sparse lists to HOST buffers (any pointer may be NULL):
