@@ -329,9 +329,16 @@ const char *sparse_lbm_last_error(void);
  * kernels', so a member's state evolves bit for bit as it would alone.  Pool
  * work runs on the pool's stream: synchronise it (any pool call that returns
  * host data does) before using a member handle directly. */
+/* A pool for members of stencil q (19 | 27) and storage (as slbm_desc) with
+ * `capacity` slots (1..65536); `stream` is a cudaStream_t or NULL.  Errors:
+ * SLBM_EINVAL (bad q, storage or capacity, NULL out), SLBM_ENOMEM,
+ * SLBM_ECUDA (no device). */
 slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream,
                              slbm_pool_t **out);
-/* Add a domain (not owned by the pool) to a free slot; SLBM_ENOMEM if full. */
+/* Add a domain (not owned by the pool) to a free slot, written to *slot.
+ * Errors: SLBM_EINVAL (NULL argument, q or storage differing from the pool's,
+ * already a member), SLBM_EUNSUPPORTED (not the sparse layout, or MRT),
+ * SLBM_ENOMEM (no free slot). */
 slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot);
 /* Remove a member after its queued pool work has finished (synchronises). */
 slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot);
@@ -381,6 +388,8 @@ slbm_status slbm_pool_set_streams(slbm_pool_t *p, int32_t n);
  * (restore them from a checkpoint).  raise == 0: wait for the pool's
  * stream, then clear the word and the latched status. */
 slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise);
+/* Wait for the pool's queued work, then release the pool (not its members,
+ * which stay valid); NULL is a no-op. */
 void slbm_pool_free(slbm_pool_t *p);
 
 #ifdef __cplusplus
