@@ -220,8 +220,10 @@ slbm_status sparse_lbm_export_lists(const slbm_t *h, int32_t *cell_voxel, int32_
 slbm_status sparse_lbm_export_codes(slbm_t *h, uint16_t *codes, int32_t *bases);
 
 /* Checkpoint / resume: raw stored PDFs (Q x S elements of the storage type,
- * bytes = Q*S*element size) plus the step counter, to or from HOST memory.
- * A resumed run continues bit-for-bit like an uninterrupted one. */
+ * bytes = Q*S*element size) plus the step counter, to or from HOST memory
+ * (caller-owned, `bytes` long).  Synchronous.  A resumed run continues
+ * bit-for-bit like an uninterrupted one.  Errors: SLBM_EINVAL (NULL
+ * argument, step < 0), SLBM_ECUDA (the copy failed). */
 slbm_status sparse_lbm_state_bytes(const slbm_t *h, int64_t *bytes);
 slbm_status sparse_lbm_get_state(const slbm_t *h, void *host, int64_t *step);
 slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
@@ -271,7 +273,9 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
  * SLBM_EDEVICE instead of touching memory out of range; 0 = fast path. */
 slbm_status sparse_lbm_set_checked(slbm_t *h, int32_t on);
 
-/* Latched device error (0 none), synchronising the stream. Clears it. */
+/* Latched device error (0 none), synchronising the stream. Clears it.
+ * Returns SLBM_EDEVICE when a code was latched (also written to *code),
+ * SLBM_EINVAL for a NULL argument, SLBM_ECUDA if the synchronisation fails. */
 slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code);
 
 /* Release everything; NULL is a no-op. */
