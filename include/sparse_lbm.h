@@ -295,8 +295,8 @@ void sparse_lbm_free(slbm_t *h);
  * results out; the call makes no cudaMalloc, cudaFree or other allocating
  * library call.
  *
- * What it computes: the compaction sparse_lbm_create uses in the
- * lexicographic order SLBM_ORDER_LEX (Sec. 3.1): cell_id[v] = rank of voxel v
+ * What it computes: the compaction in the
+ * lexicographic order SLBM_ORDER_LEX that sparse_lbm_create uses: cell_id[v] = rank of voxel v
  * among fluid voxels (flag 0) in ascending voxel id, or -1; cell_voxel[k] = voxel id of fluid cell k; *n_fluid = count.
  * All pointers are DEVICE pointers: flags[n_voxels] (uint8), cell_id[n_voxels],
  * cell_voxel[capacity >= number of fluid voxels], n_fluid[1] (int32).  The work
@@ -307,9 +307,12 @@ void sparse_lbm_free(slbm_t *h);
  * the library (256 KiB), which every GPU that loads the library holds until
  * the process exits.  All calls share it and it keeps the last call's
  * contents; each call overwrites what it reads first.  Calls that overlap on
- * the GPU (e.g. on two streams at once) race on it: serialise them.  The first
- * call on each device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * the GPU (e.g. on two streams at once) race on it: serialise them.  Every
+ * call made outside a stream capture looks up the array's device address on
+ * the current device (so a device reset that reloads the library's module is
+ * followed); a call made while `stream` is being captured uses the address
+ * that the last call outside capture found on that device, so make one call
+ * on the device before any capture (SLBM_ECUDA otherwise).
  *
  * Errors: SLBM_EINVAL if n_voxels < 0, n_voxels > SLBM_NOALLOC_MAX_VOXELS or a
  * needed pointer is NULL (nothing is launched); SLBM_ECUDA if the device or a

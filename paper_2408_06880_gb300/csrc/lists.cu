@@ -528,12 +528,15 @@ static_assert(NOALLOC_MAX_TILES * SCAN_TILE == SLBM_NOALLOC_MAX_VOXELS, "limit m
 // uses before reading them, so nothing needs clearing between calls.
 static __device__ __align__(256) int32_t g_noalloc_tiles[NOALLOC_MAX_TILES];
 
-// Device address of g_noalloc_tiles per device, looked up once per device
-// (the host-side name of the array is not a device address).
+// Device address of g_noalloc_tiles per device.  The host-side name of the
+// array is not a device address, so every call made outside a stream capture
+// looks the address up with its device current (a device reset that reloads
+// the module moves the array); a call inside a capture, where the lookup is
+// not allowed, uses the address the last call outside capture found.
 static std::mutex g_noalloc_mu;
 static int32_t *g_noalloc_addr[128] = {};
 
-static int noalloc_scratch(int32_t **out) {
+static int noalloc_scratch(cudaStream_t st, int32_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= 128) {
@@ -541,8 +544,16 @@ static int noalloc_scratch(int32_t **out) {
         set_error(SLBM_ECUDA, "sparse_lbm_compact_noalloc: no current CUDA device");
         return -1;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(SLBM_ECUDA, std::string("sparse_lbm_compact_noalloc: cudaStreamIsCapturing: ") +
+                                  cudaGetErrorString(e));
+        return -1;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
         if (e != cudaSuccess || !p) {
@@ -552,6 +563,10 @@ static int noalloc_scratch(int32_t **out) {
             return -1;
         }
         g_noalloc_addr[dev] = (int32_t *)p;
+    } else if (!g_noalloc_addr[dev]) {
+        set_error(SLBM_ECUDA, "sparse_lbm_compact_noalloc: first call on this device made during a stream "
+                              "capture (call it once outside capture first)");
+        return -1;
     }
     *out = g_noalloc_addr[dev];
     return 0;
@@ -571,9 +586,9 @@ extern "C" slbm_status sparse_lbm_compact_noalloc(const uint8_t *flags, int64_t 
         set_error(SLBM_EINVAL, "sparse_lbm_compact_noalloc: null device pointer");
         return SLBM_EINVAL;
     }
-    int32_t *tiles = nullptr;
-    if (noalloc_scratch(&tiles)) return SLBM_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    int32_t *tiles = nullptr;
+    if (noalloc_scratch(st, &tiles)) return SLBM_ECUDA;
     cudaError_t e;
     if (n_voxels == 0) {
         e = cudaMemsetAsync(n_fluid, 0, sizeof(int32_t), st);

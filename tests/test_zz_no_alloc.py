@@ -11,8 +11,10 @@ The test calls the entry point through the C ABI twice in a row, on two
 different geometries (so the shared scratch holds the first call's contents
 when the second starts), and checks both results against the compaction of the
 existing path (sparse_lbm_create + sparse_lbm_export_lists), bit for bit, as
-all integer outputs in this suite are compared.  It also checks that a size
-above the stated maximum is refused before anything is launched.  The file is
+all integer outputs in this suite are compared; checks voxel counts that end
+in a partial scan tile against a sequential scan; checks that a call leaves the
+device's free memory unchanged; and checks that a size above the stated
+maximum is refused before anything is launched.  The file is
 named to be collected last so a failing run that stops at the first failure
 has run every other test first; it also passes on its own in a fresh process.
 """
@@ -63,6 +65,50 @@ def test_noalloc_compaction_matches_existing_path_twice_in_a_row():
         fluid = g.flags.reshape(-1) == 0
         assert np.all(cid[~fluid] == -1)
         assert np.array_equal(cid[cvx], np.arange(nf))
+
+
+def test_noalloc_ragged_last_tile_matches_a_sequential_scan():
+    # voxel counts that are not whole 4096-voxel scan tiles: the partial last
+    # tile of this path, compared with the plain sequential numbering
+    torch = pytest.importorskip("torch")
+    from paper_2408_06880_gb300 import _capi as capi
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(7)
+    for n in (33 * 31 * 29, 4096 * 3 + 17, 4095, 1):
+        flags = (rng.random(n) < 0.4).astype(np.uint8)      # 60 % fluid (flag 0)
+        nf, cid, cvx = _noalloc(torch, capi, flags, stream)
+        ref = np.flatnonzero(flags == 0)
+        assert nf == ref.size
+        assert np.array_equal(cvx, ref)
+        want = np.full(n, -1, np.int64)
+        want[ref] = np.arange(ref.size)
+        assert np.array_equal(cid, want)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    # the defining property: a call (after a first one has loaded the kernels)
+    # changes neither the device's free memory nor PyTorch's allocations
+    torch = pytest.importorskip("torch")
+    from paper_2408_06880_gb300 import _capi as capi
+    stream = torch.cuda.Stream()
+    g = G.boolean_spheres(64, 0.5, 5)
+    n = g.flags.size
+    flags = torch.from_numpy(g.flags.reshape(-1)).to("cuda")
+    cell_id = torch.empty(n, dtype=torch.int32, device="cuda")
+    cell_voxel = torch.empty(n, dtype=torch.int32, device="cuda")
+    n_fluid = torch.empty(1, dtype=torch.int32, device="cuda")
+    args = (flags.data_ptr(), n, cell_id.data_ptr(), cell_voxel.data_ptr(), n_fluid.data_ptr(), stream.cuda_stream)
+    capi.check(capi.lib().sparse_lbm_compact_noalloc(*args))
+    stream.synchronize()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    capi.check(capi.lib().sparse_lbm_compact_noalloc(*args))
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert int(n_fluid.item()) == int(np.count_nonzero(g.flags == 0))
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
