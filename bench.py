@@ -85,6 +85,13 @@ def parse():
                          "advances CHUNKS chunks per tick ('none': one lockstep lane)")
     ap.add_argument("--group-mb", type=float, default=None,
                     help="serve mode: L2 group size of the pool in MiB (0 = one group; default: the library's)")
+    ap.add_argument("--precision", default="plan", choices=["plan", "none"],
+                    help="serve mode, 16-bit storage: 'plan' hands each solve off to FP32 storage once its "
+                         "relative change per chunk falls below 3e-3 (and rescales while in 16 bits); 'none' "
+                         "solves in 16 bits throughout")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="default run: requests of the serving summary (0 skips it)")
+    ap.add_argument("--serve-repeats", type=int, default=3, help="default run: repeats of the serving summary")
     a = ap.parse_args()
     if a.lbm_steps % 2:
         raise SystemExit("--lbm-steps must be even (whole AA pairs)")
@@ -266,6 +273,8 @@ def run_ours(a, rank, world):
         out["e2e"] = bench_e2e(a, P)
         if world == 1:
             out["cpu_baseline"] = cpu_baseline(a, [g for _, g, _ in doms])
+            if a.serve_requests > 0:
+                out["serve"] = bench_serve_summary(a, P)
     for _, _, d in doms:
         d.close()
     return out
@@ -528,6 +537,115 @@ def serve_requests(n, max_steps):
     return reqs
 
 
+ORACLE_SERVING = os.path.join(ROOT, "tests", "golden", "serving16_oracle.json")
+
+
+def oracle_permeability_errors(results):
+    """Relative permeability error of served results against the FP64
+    oracle's values stored in tests/golden/serving16_oracle.json (written by
+    tests/golden/make_oracle_fixtures.py: the oracle's sum of u_x after every
+    100 steps of the first 16 requests of edge 64 or 96), compared at the
+    result's own step count (the oracle's last stored value when the result
+    ran longer).  {} when the file is absent."""
+    try:
+        with open(ORACLE_SERVING) as f:
+            ref = {r["rid"]: r for r in json.load(f)["requests"]}
+    except Exception:
+        return {}
+    out = {}
+    for r in results:
+        o = ref.get(r.rid)
+        if o is None or r.permeability is None or r.steps <= 0:
+            continue
+        j = min(r.steps // 100, len(o["sum_ux"])) - 1
+        k_o = o["nu"] * (o["sum_ux"][j] / o["n_voxels"]) / 1e-6
+        out[r.rid] = abs(r.permeability / k_o - 1)
+    return out
+
+
+def make_executor(a, P, storage, lanes_spec=None):
+    from paper_2408_06880_gb300.serving import GpuExecutor, Precision
+    spec = a.lanes if lanes_spec is None else lanes_spec
+    lanes = None
+    if spec != "none":
+        cells, chunks = (int(x) for x in spec.split(":"))
+        lanes = ((cells, chunks), (None, 1, a.large_cap or None))
+    prec = Precision() if storage != P.FP32 and a.precision == "plan" else None
+    return GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph),
+                       group_bytes=None if a.group_mb is None else int(a.group_mb * 2 ** 20),
+                       streams=a.pool_streams, lanes=lanes, precision=prec)
+
+
+def bench_serve_summary(a, P, storages=("fp32", "fp16")):
+    """Bounded serving measurement for the default line: the first
+    `--serve-requests` requests of the stream as a closed batch through the
+    continuous-batching server, and the same requests solved one at a time,
+    per storage (16-bit storage with the FP32 hand-off plan), repeated
+    `--serve-repeats` times; medians and the spread of the served /
+    one-at-a-time ratio.  Accuracy: each 16-bit result against the FP32
+    result of the same request, and against the FP64 oracle's stored values
+    for the requests of the oracle subset."""
+    import torch
+    from paper_2408_06880_gb300.serving import Server, solve_alone
+    reqs = serve_requests(a.requests if a.mode == "serve" else a.serve_requests, a.max_steps)
+    budget = int(a.budget_gb * 2 ** 30)
+    out = {"requests": len(reqs), "repeats": a.serve_repeats,
+           "what": "closed batch of the first requests of the permeability stream (D3Q19 TRT, F = 1e-6, "
+                   "converged to 1e-6 relative change of mean u_x per 100 steps), served with continuous "
+                   "batching and solved one at a time; 16-bit storage handed off to FP32 (precision plan)"}
+    k_by = {}
+    for name in storages:
+        storage = {"fp32": P.FP32, "fp16": P.FP16, "bf16": P.BF16}[name]
+        served, seq, ratio = [], [], []
+        for _ in range(max(1, a.serve_repeats)):
+            ex = make_executor(a, P, storage)
+            try:
+                res, st = Server(ex, budget, chunk=100).run(reqs, realtime=False)
+                ticks = {r.rid: ex.tick_chunks(r) for r in reqs}
+            finally:
+                ex.close()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            alone = [solve_alone(r, storage=storage, precision=ex.precision, tick=ticks[r.rid]) for r in reqs]
+            wall = time.perf_counter() - t0
+            lat = np.array([r.latency for r in alone])
+            sq = {"solves_per_s": len(alone) / wall, "latency_p50_s": float(np.percentile(lat, 50)),
+                  "latency_p99_s": float(np.percentile(lat, 99))}
+            served.append(st)
+            seq.append(sq)
+            ratio.append(st["solves_per_s"] / sq["solves_per_s"])
+        med = lambda xs, key: float(np.median([x[key] for x in xs]))  # noqa: E731
+        k_alone = {r.rid: r.permeability for r in alone}
+        row = {"served_solves_per_s": round(med(served, "solves_per_s"), 4),
+               "served_p50_s": round(med(served, "latency_p50_s"), 4),
+               "served_p99_s": round(med(served, "latency_p99_s"), 4),
+               "one_at_a_time_solves_per_s": round(med(seq, "solves_per_s"), 4),
+               "one_at_a_time_p50_s": round(med(seq, "latency_p50_s"), 4),
+               "one_at_a_time_p99_s": round(med(seq, "latency_p99_s"), 4),
+               "served_over_one_at_a_time": {"median": round(float(np.median(ratio)), 4),
+                                             "min": round(min(ratio), 4), "max": round(max(ratio), 4)},
+               "converged": int(sum(r.converged for r in res)), "solved": st["solved"],
+               "served_equals_alone": all(r.permeability == k_alone[r.rid] and r.steps == a_.steps
+                                          for r in res for a_ in alone if a_.rid == r.rid and r.error is None),
+               "low_precision_step_share": round(st["low_precision_step_share"], 4)}
+        k_by[name] = {r.rid: r.permeability for r in res if r.error is None}
+        oerr = oracle_permeability_errors(res)
+        if oerr:
+            row["vs_fp64_oracle"] = {"requests": len(oerr), "max_rel_error": float(max(oerr.values())),
+                                     "median_rel_error": float(np.median(list(oerr.values())))}
+        out[name] = row
+    if "fp32" in k_by:
+        for name in storages:
+            if name == "fp32":
+                continue
+            e = [abs(k_by[name][i] / k_by["fp32"][i] - 1) for i in k_by[name] if i in k_by["fp32"]]
+            out[name]["vs_fp32_permeability"] = {"max_rel_error": float(max(e)), "median_rel_error":
+                                                 float(np.median(e))}
+            out[name]["served_vs_fp32_served"] = round(out[name]["served_solves_per_s"] /
+                                                       out["fp32"]["served_solves_per_s"], 4)
+    return out
+
+
 def run_serve(a):
     """Serve mode: continuous batching of the request stream (closed batch or
     Poisson arrivals), optionally against one-at-a-time solves.  Under
@@ -536,7 +654,7 @@ def run_serve(a):
     import torch
     import paper_2408_06880_gb300 as P
     from paper_2408_06880_gb300 import replicas
-    from paper_2408_06880_gb300.serving import GpuExecutor, serve_replicas, solve_alone
+    from paper_2408_06880_gb300.serving import serve_replicas, solve_alone
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     rank, world = replicas.rank_world()
     storage = {"fp32": P.FP32, "fp16": P.FP16, "bf16": P.BF16}[a.storage]
@@ -551,13 +669,8 @@ def run_serve(a):
                       "pool_graph": bool(a.pool_graph), "group_mb": a.group_mb,
                       "pool_streams": a.pool_streams, "lanes": a.lanes, "large_cap": a.large_cap,
                       "parallelism": f"request replicas x{world}" if world > 1 else "single GPU"}}
-    lanes = None
-    if a.lanes != "none":
-        cells, chunks = (int(x) for x in a.lanes.split(":"))
-        lanes = ((cells, chunks), (None, 1, a.large_cap or None))
-    ex = GpuExecutor(Q, storage, capacity=a.capacity, graph=bool(a.pool_graph),
-                     group_bytes=None if a.group_mb is None else int(a.group_mb * 2 ** 20),
-                     streams=a.pool_streams, lanes=lanes)
+    ex = make_executor(a, P, storage)
+    out["config"]["precision"] = "fp32 hand-off plan" if ex.precision is not None else "none"
     budget = int(a.budget_gb * 2 ** 30)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
     clocks.start()
@@ -575,14 +688,22 @@ def run_serve(a):
             r.arrival = float(ti)
         _, st_p = serve_replicas(ex, reqs, budget, realtime=True, chunk=100)
         out["poisson"] = dict(st_p, rate_per_s=rate)
+    ticks = {r.rid: ex.tick_chunks(r) for r in reqs}
+    prec = ex.precision
     ex.close()
-    out["results"] = [{"rid": r.rid, "k": r.permeability, "steps": r.steps, "converged": r.converged,
-                       "latency_s": round(r.latency, 4), "error": r.error} for r in sorted(res, key=lambda r: r.rid)]
+    out["results"] = [{"rid": r.rid, "k": r.permeability, "steps": r.steps, "low_precision_steps": r.low_steps,
+                       "converged": r.converged, "latency_s": round(r.latency, 4), "error": r.error}
+                      for r in sorted(res, key=lambda r: r.rid)]
+    oerr = oracle_permeability_errors(res)
+    if oerr:
+        out["vs_fp64_oracle"] = {"requests": len(oerr), "max_rel_error": float(max(oerr.values())),
+                                 "median_rel_error": float(np.median(list(oerr.values()))),
+                                 "per_request": {str(k): v for k, v in sorted(oerr.items())}}
     if a.sequential:
         mine = replicas.shard(reqs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        alone = [solve_alone(r, storage=storage) for r in mine]
+        alone = [solve_alone(r, storage=storage, precision=prec, tick=ticks[r.rid]) for r in mine]
         wall = time.perf_counter() - t0
         sps, _, wall_max = replicas.job_rate(len(alone), wall)
         # service times and one-at-a-time FIFO latencies per rank (each rank

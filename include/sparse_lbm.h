@@ -182,6 +182,37 @@ slbm_status sparse_lbm_macroscopic(slbm_t *h, float *rho, float *u, int32_t orde
  * is not finite. */
 slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem);
 
+/* Domain sums plus two maxima, for the convergence and stability checks of a
+ * solve and for choosing the storage scale of FP16/BF16 populations:
+ * out[0..4] = exactly the values of sparse_lbm_reduce (the same bits);
+ * out[5] = the largest |f_i - w_i| over the stored populations (shifted,
+ * unscaled; every slot of every fluid cell at either AA parity);
+ * out[6] = the largest speed |u| (Eq. 1, Guo half-force velocity) over fluid
+ * cells.  Both maxima are exact (the order of a maximum does not matter) and
+ * a NaN anywhere makes them NaN.  mem as sparse_lbm_reduce; host mode
+ * synchronises and returns SLBM_EDIVERGED (after writing out) when a value is
+ * not finite or out[6] > 0.3 (beyond the stability bound of the lattice).
+ * Device mode writes 7 doubles asynchronously.  Errors: SLBM_EINVAL (NULL
+ * argument, bad mem), SLBM_ECUDA. */
+slbm_status sparse_lbm_reduce_ext(slbm_t *h, double *out, int32_t mem);
+
+/* Change the storage of the populations in place (the paper's zero-centred
+ * storage, Sec. 4, kept in every format): every stored value v of the current
+ * format A with scale s_a becomes pack_B(raw_A(v) * 2^(s_b - s_a)) in format
+ * `storage` with scale `scale_exp` (ignored for SLBM_FP32, which has none).
+ * FP16/BF16 -> FP32 and a power-of-two rescale within FP16/BF16 are exact
+ * for values that stay normal numbers; FP32 -> FP16/BF16 rounds to nearest
+ * even like every store of the stepping kernels.  The state keeps its step
+ * and parity, so stepping continues from it.  A change of element size
+ * allocates the new array (through the domain's allocator) before freeing
+ * the old one, so a failure leaves the domain unchanged.  Launch shapes are
+ * reset to the defaults of the new storage; cached graphs are dropped.
+ * Synchronous.  Errors: SLBM_EINVAL (bad storage, scale_exp outside
+ * [-40, 40], the domain is a pool member -- slbm_pool_remove it first -- or
+ * the converted values would overflow the target format), SLBM_EDIVERGED
+ * (a stored value is not finite), SLBM_ENOMEM, SLBM_ECUDA. */
+slbm_status sparse_lbm_set_storage(slbm_t *h, int32_t storage, int32_t scale_exp);
+
 /* Set the state to the equilibrium of given fields (Eq. 6): rho (n floats)
  * and u (3 x n, component-major) in cell or voxel order, device or host
  * memory.  NULL rho means 1, NULL u means 0.  Resets the step counter to 0. */
@@ -278,7 +309,8 @@ slbm_status sparse_lbm_set_checked(slbm_t *h, int32_t on);
  * SLBM_EINVAL for a NULL argument, SLBM_ECUDA if the synchronisation fails. */
 slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code);
 
-/* Release everything; NULL is a no-op. */
+/* Release everything (a pool that still holds the domain loses it as a
+ * member, after its queued work); NULL is a no-op. */
 void sparse_lbm_free(slbm_t *h);
 
 /* Largest voxel count sparse_lbm_compact_noalloc accepts (65536 scan tiles of
@@ -359,6 +391,10 @@ slbm_status slbm_pool_step(slbm_pool_t *p, int32_t k, int32_t use_graph);
  * member.  Host mode returns SLBM_EABORTED if an abort was raised since the
  * last clear. */
 slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem);
+/* As slbm_pool_reduce with sparse_lbm_reduce_ext's 7 values per slot
+ * (capacity x 7 doubles; free slots are zero); host mode returns
+ * SLBM_EABORTED like slbm_pool_reduce and does not test the values. */
+slbm_status slbm_pool_reduce_ext(slbm_pool_t *p, double *out, int32_t mem);
 /* Launch variant.  ctas_per_sm == 0 (default): tile grid -- one CTA of 128
  * threads per tile of the concatenated cell lists (256-cell tiles for the even
  * step, 128-cell tiles for the odd step); each launch carries its group's
@@ -396,7 +432,7 @@ slbm_status slbm_pool_set_streams(slbm_pool_t *p, int32_t n);
  * stream, then clear the word and the latched status. */
 slbm_status slbm_pool_abort(slbm_pool_t *p, int32_t raise);
 /* Wait for the pool's queued work, then release the pool (not its members,
- * which stay valid); NULL is a no-op. */
+ * which stay valid and are no longer pool members); NULL is a no-op. */
 void slbm_pool_free(slbm_pool_t *p);
 
 #ifdef __cplusplus

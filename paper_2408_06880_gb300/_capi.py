@@ -60,6 +60,8 @@ SIGNATURES = {
     "sparse_lbm_step_graph": (_st, [_vp, _i32]),
     "sparse_lbm_macroscopic": (_st, [_vp, _vp, _vp, _i32, _i32]),
     "sparse_lbm_reduce": (_st, [_vp, _vp, _i32]),
+    "sparse_lbm_reduce_ext": (_st, [_vp, _vp, _i32]),
+    "sparse_lbm_set_storage": (_st, [_vp, _i32, _i32]),
     "sparse_lbm_init_equilibrium": (_st, [_vp, _vp, _vp, _i32, _i32]),
     "sparse_lbm_info": (_st, [_vp, C.POINTER(Info)]),
     "sparse_lbm_export_lists": (_st, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -79,6 +81,7 @@ SIGNATURES = {
     "slbm_pool_remove": (_st, [_vp, _i32]),
     "slbm_pool_step": (_st, [_vp, _i32, _i32]),
     "slbm_pool_reduce": (_st, [_vp, _vp, _i32]),
+    "slbm_pool_reduce_ext": (_st, [_vp, _vp, _i32]),
     "slbm_pool_set_launch": (_st, [_vp, _i32, _i32]),
     "slbm_pool_abort": (_st, [_vp, _i32]),
     "slbm_pool_set_split": (_st, [_vp, _i64]),

@@ -95,6 +95,20 @@ CollideParams Domain::collide_params() const {
     return p;
 }
 
+// Default launch shapes of a domain's storage.  Even step: cells collided in
+// pairs (measured faster except for FP16 MRT and untimed BF16); FP16 D3Q27
+// from bulk-staged tiles.  Odd step: 128 x 1 with the L2 index prefetch.
+static void default_shapes(Domain &d) {
+    d.shape[0] = LaunchShape{64, 2, 0};
+    d.shape[1] = LaunchShape{128, 1, 2};
+    if (d.layout == SLBM_LAYOUT_SPARSE && d.storage != SLBM_BF16) {
+        if (d.op != SLBM_MRT)
+            d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
+        else if (d.storage == SLBM_FP32)
+            d.shape[0] = LaunchShape{64, 2, 2};
+    }
+}
+
 // d'Humieres et al. (2002) rates with omega on the stress moments.
 static void default_mrt_rates(Domain &d) {
     const double w = d.omega_p;
@@ -272,14 +286,7 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (d.op == SLBM_MRT) default_mrt_rates(d);
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
-    // even step: cells collided in pairs (measured faster except for FP16 MRT
-    // and untimed BF16); FP16 D3Q27 from bulk-staged tiles
-    if (d.layout == SLBM_LAYOUT_SPARSE && d.storage != SLBM_BF16) {
-        if (d.op != SLBM_MRT)
-            d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
-        else if (d.storage == SLBM_FP32)
-            d.shape[0] = LaunchShape{64, 2, 2};
-    }
+    default_shapes(d);
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -332,8 +339,8 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (!rc && rows_bytes) rc = cx.check(cudaMemsetAsync(d.pdf.p, 0, rows_bytes, d.stream), "memset pdf");
     if (!rc && d.pull()) rc = cx.alloc(d.pdf2, rows_bytes);
     if (!rc && d.pull() && rows_bytes) rc = cx.check(cudaMemsetAsync(d.pdf2.p, 0, rows_bytes, d.stream), "memset pdf2");
-    if (!rc) rc = cx.alloc(d.red_partial, std::max<int64_t>(d.red_chunks(), 1) * 5 * sizeof(double));
-    if (!rc) rc = cx.alloc(d.red_out, 5 * sizeof(double));
+    if (!rc) rc = cx.alloc(d.red_partial, std::max<int64_t>(d.red_chunks(), 1) * (5 * sizeof(double) + 2 * sizeof(float)));
+    if (!rc) rc = cx.alloc(d.red_out, 8 * sizeof(double));
     if (!rc) rc = cx.alloc(d.err, sizeof(int32_t));
     if (!rc) rc = cx.check(cudaMemsetAsync(d.err.p, 0, sizeof(int32_t), d.stream), "memset err");
     if (!rc) rc = cx.check(cudaStreamSynchronize(d.stream), "create sync");
@@ -425,6 +432,41 @@ slbm_status sparse_lbm_reduce(slbm_t *h, double *out, int32_t mem) {
     if (e != cudaSuccess) return cuda_err(e, "reduce");
     for (int c = 0; c < 5; ++c)
         if (!std::isfinite(out[c])) return err(SLBM_EDIVERGED, "domain sums are not finite");
+    return ok();
+}
+
+slbm_status sparse_lbm_reduce_ext(slbm_t *h, double *out, int32_t mem) {
+    const Range range_("slbm reduce ext");
+    if (!h || !out) return err(SLBM_EINVAL, "null argument");
+    Domain &d = h->d;
+    if (mem == SLBM_MEM_DEVICE) {
+        const cudaError_t e = launch_reduce_ext(d, out, d.stream);
+        return e == cudaSuccess ? ok() : cuda_err(e, "reduce_ext");
+    }
+    if (mem != SLBM_MEM_HOST) return err(SLBM_EINVAL, "bad mem");
+    cudaError_t e = launch_reduce_ext(d, (double *)d.red_out.p, d.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d.red_out.p, 7 * sizeof(double), cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+    if (e != cudaSuccess) return cuda_err(e, "reduce_ext");
+    for (int c = 0; c < 7; ++c)
+        if (!std::isfinite(out[c])) return err(SLBM_EDIVERGED, "domain sums or maxima are not finite");
+    if (out[6] > 0.3) return err(SLBM_EDIVERGED, "a cell's speed exceeds 0.3");
+    return ok();
+}
+
+slbm_status sparse_lbm_set_storage(slbm_t *h, int32_t storage, int32_t scale_exp) {
+    const Range range_("slbm set storage");
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    if (storage < SLBM_FP32 || storage > SLBM_BF16) return err(SLBM_EINVAL, "storage must be 0, 1 or 2");
+    if (scale_exp < -40 || scale_exp > 40) return err(SLBM_EINVAL, "scale_exp must lie in [-40, 40]");
+    Domain &d = h->d;
+    if (!d.pools.empty()) return err(SLBM_EINVAL, "the domain is a pool member: remove it from its pool first");
+    const int new_s = storage == SLBM_FP32 ? 0 : scale_exp;
+    if (storage == d.storage && new_s == d.scale_exp) return ok();
+    Ctx cx = d.ctx();
+    if (convert_storage(cx, d, storage, new_s)) return err(cx.status == SLBM_OK ? SLBM_ECUDA : cx.status, g_msg);
+    default_shapes(d);
+    drop_graphs(d);
     return ok();
 }
 
@@ -635,6 +677,8 @@ slbm_status sparse_lbm_device_error(slbm_t *h, int32_t *code) {
 void sparse_lbm_free(slbm_t *h) {
     if (!h) return;
     Domain &d = h->d;
+    for (::slbm_pool *p : d.pools) pool_forget_member(p, h);   // no pool keeps a dangling member
+    d.pools.clear();
     cudaStreamSynchronize(d.stream);
     drop_graphs(d);
     release_all(d);

@@ -6,6 +6,7 @@
 #include <string>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -75,8 +76,8 @@ struct Domain {
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity
     int64_t n_bcells = 0;
     DevBuf mask;                       // per-voxel link mask (dense)
-    DevBuf red_partial;                // per-chunk FP64 partial sums
-    DevBuf red_out;                    // 5 doubles
+    DevBuf red_partial;                // per-chunk FP64 partial sums (5 doubles), then per-chunk maxima (2 floats)
+    DevBuf red_out;                    // 8 doubles
     DevBuf err;                        // latched device error word
     // execution
     cudaStream_t stream = nullptr;
@@ -86,6 +87,7 @@ struct Domain {
     int64_t device_bytes = 0;
     LaunchShape shape[2] = {{64, 2, 0}, {128, 1, 2}};
     bool checked = false;
+    std::vector<::slbm_pool *> pools;  // pools that hold this domain as a member
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (n, parity) -> exec
 
     int bytes_per_pdf() const { return storage == SLBM_FP32 ? 4 : 2; }
@@ -127,8 +129,14 @@ cudaError_t domain_graph(Domain &d, int32_t n, cudaGraphExec_t *out);
 // macro.cu
 cudaError_t launch_macroscopic(const Domain &d, float *rho, float *u, int order, cudaStream_t st);
 cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st);
+// the five sums plus max |f_i - w_i| and max |u| (7 doubles)
+cudaError_t launch_reduce_ext(const Domain &d, double *out_dev, cudaStream_t st);
 cudaError_t launch_init_equilibrium(const Domain &d, const float *rho, const float *u, int order,
                                     cudaStream_t st);
+// convert.cu: stored populations to another storage format / scale
+int convert_storage(Ctx &cx, Domain &d, int storage, int scale_exp);
+// pool.cu: take a domain that is being freed out of a pool's member slots
+void pool_forget_member(::slbm_pool *p, ::slbm_domain *h);
 // dense.cu
 int build_dense_mask(Ctx &cx, Domain &d, const uint8_t *d_flags);
 cudaError_t launch_dense_step(const Domain &d, int parity, cudaStream_t st);

@@ -90,15 +90,48 @@ struct DenseView {
 };
 
 // ------------------------------------------------------------ kernels
+// Largest of two values, NaN if either is NaN (fmaxf would drop it).
+__device__ __forceinline__ float nan_max(float a, float b) {
+    return a != a ? a : (b != b ? b : fmaxf(a, b));
+}
+
+// Maximum over the block of two floats (exact, so independent of the order;
+// a NaN wins); thread 0 writes them to out[0..1].
+__device__ __forceinline__ void block_max2_to(float a, float b, float *out) {
+    __shared__ float sm[32][2];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = nan_max(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = nan_max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm[warp][0] = a;
+        sm[warp][1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = nan_max(a, sm[w][0]);
+            b = nan_max(b, sm[w][1]);
+        }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
 // One block per chunk of RED_CHUNK cells; thread t takes cells
 // chunk*RED_CHUNK + j*RED_THREADS + t, j = 0..RED_CELLS_PER_THREAD-1, in
-// that order.  Writes optional fields and the chunk's five FP64 partials.
+// that order.  Writes optional fields and the chunk's five FP64 partials;
+// with `maxes`, also the chunk's largest |f_i - w_i| over the populations it
+// read (unscaled) and largest speed |u| (a NaN anywhere makes them NaN).
 template <int Q, class St, class View>
 __global__ void __launch_bounds__(RED_THREADS) macro_reduce_kernel(const typename St::T *pdf, View view,
                                                                    bool odd, CollideParams p, float *rho_out,
                                                                    float *u_out, int64_t u_stride, int order,
-                                                                   double *partial) {
+                                                                   double *partial, float *maxes = nullptr) {
     double acc[5] = {0, 0, 0, 0, 0};
+    float gmax = 0.f, umax = 0.f;
     const int32_t base = blockIdx.x * RED_CHUNK + threadIdx.x;
 #pragma unroll 1
     for (int j = 0; j < RED_CELLS_PER_THREAD; ++j) {
@@ -116,6 +149,11 @@ __global__ void __launch_bounds__(RED_THREADS) macro_reduce_kernel(const typenam
         acc[2] += (double)my;
         acc[3] += (double)mz;
         acc[4] += (double)ux;
+        if (maxes) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) gmax = nan_max(gmax, fabsf(g[i]));
+            umax = nan_max(umax, sqrtf(ux * ux + uy * uy + uz * uz));
+        }
         const int64_t o = order == SLBM_ORDER_VOXELS ? (int64_t)view.voxel(k) : (int64_t)k;
         if (rho_out) rho_out[o] = rho;
         if (u_out) {
@@ -125,6 +163,24 @@ __global__ void __launch_bounds__(RED_THREADS) macro_reduce_kernel(const typenam
         }
     }
     if (partial) block_sum5_to(acc, partial + (int64_t)blockIdx.x * 5);
+    if (maxes) block_max2_to(gmax, umax, maxes + 2 * (int64_t)blockIdx.x);
+}
+
+// One block: out[c] = max over chunks of maxes[2*chunk + c], c = 0, 1 (NaN
+// if any is NaN), as doubles.
+__global__ void reduce_max_partials_kernel(const float *maxes, int64_t chunks, double *out) {
+    float a = 0.f, b = 0.f;
+    for (int64_t j = threadIdx.x; j < chunks; j += blockDim.x) {
+        a = nan_max(a, maxes[2 * j]);
+        b = nan_max(b, maxes[2 * j + 1]);
+    }
+    __shared__ float r[2];
+    block_max2_to(a, b, r);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = (double)r[0];
+        out[1] = (double)r[1];
+    }
 }
 
 template <int Q, class St, class View>
@@ -204,6 +260,29 @@ cudaError_t launch_reduce(const Domain &d, double *out_dev, cudaStream_t st) {
     });
     if (e != cudaSuccess) return e;
     reduce_partials_kernel<<<1, RED_THREADS, 0, st>>>((const double *)d.red_partial.p, chunks, out_dev);
+    return cudaGetLastError();
+}
+
+// The five sums into out_dev[0..4] (the same bits as launch_reduce) and the
+// two maxima into out_dev[5..6].  The chunk maxima sit behind the sums'
+// partials in red_partial.
+cudaError_t launch_reduce_ext(const Domain &d, double *out_dev, cudaStream_t st) {
+    const int64_t chunks = d.red_chunks();
+    if (chunks == 0) return cudaMemsetAsync(out_dev, 0, 7 * sizeof(double), st);
+    const bool odd = d.pull() ? d.step > 0 : (d.step & 1);
+    const CollideParams p = d.collide_params();
+    double *partial = (double *)d.red_partial.p;
+    float *maxes = (float *)(partial + 5 * chunks);
+    cudaError_t e = with_types(d, [&](auto qtag, auto st_t, auto view) -> cudaError_t {
+        constexpr int Q = decltype(qtag)::value;
+        using St = decltype(st_t);
+        macro_reduce_kernel<Q, St><<<(unsigned)chunks, RED_THREADS, 0, st>>>(
+            (const typename St::T *)d.cur_pdf(), view, odd, p, nullptr, nullptr, 0, 0, partial, maxes);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    reduce_partials_kernel<<<1, RED_THREADS, 0, st>>>(partial, chunks, out_dev);
+    reduce_max_partials_kernel<<<1, RED_THREADS, 0, st>>>(maxes, chunks, out_dev + 5);
     return cudaGetLastError();
 }
 

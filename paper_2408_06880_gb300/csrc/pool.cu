@@ -644,6 +644,20 @@ cudaError_t launch_one(slbm_pool *p, int32_t t, const slbm_pool::Group *g) {
 
 }  // namespace
 
+namespace slbm {
+
+void pool_forget_member(::slbm_pool *p, ::slbm_domain *h) {
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);   // queued pool work on the member ends first
+    for (auto &m : p->members)
+        if (m == h) {
+            m = nullptr;
+            p->dirty = true;
+        }
+}
+
+}  // namespace slbm
+
 extern "C" {
 
 slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void *stream, slbm_pool_t **out) {
@@ -672,7 +686,7 @@ slbm_status slbm_pool_create(int32_t q, int32_t storage, int32_t capacity, void 
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tab, (size_t)capacity * sizeof(PoolEntry));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_hdr, sizeof(PoolHeader));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_red, (size_t)capacity * 5 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_red, (size_t)capacity * 7 * sizeof(double));
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&p->h_abort, sizeof(int32_t), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *p->h_abort = 0;
@@ -708,6 +722,7 @@ slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot) {
             // order the domain's own stream before the pool's
             cudaStreamSynchronize(d.stream);
             p->members[s] = h;
+            h->d.pools.push_back(p);
             p->dirty = true;
             *slot = s;
             set_error(SLBM_OK, "");
@@ -720,6 +735,9 @@ slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot) {
 slbm_status slbm_pool_remove(slbm_pool_t *p, int32_t slot) {
     if (!p || slot < 0 || slot >= p->capacity || !p->members[slot]) return perr(SLBM_EINVAL, "bad slot");
     const cudaError_t e = cudaStreamSynchronize(p->stream);   // member work done before it leaves
+    std::vector<slbm_pool *> &ps = p->members[slot]->d.pools;
+    auto it = std::find(ps.begin(), ps.end(), p);
+    if (it != ps.end()) ps.erase(it);
     p->members[slot] = nullptr;
     p->dirty = true;
     if (e != cudaSuccess) return pcuda(e, "pool remove");
@@ -837,6 +855,30 @@ slbm_status slbm_pool_reduce(slbm_pool_t *p, double *out, int32_t mem) {
     return SLBM_OK;
 }
 
+slbm_status slbm_pool_reduce_ext(slbm_pool_t *p, double *out, int32_t mem) {
+    const Range range_("slbm pool reduce ext");
+    if (!p || !out) return perr(SLBM_EINVAL, "null argument");
+    if (mem != SLBM_MEM_DEVICE && mem != SLBM_MEM_HOST) return perr(SLBM_EINVAL, "bad mem");
+    cudaError_t e = cudaSuccess;
+    double *dev_out = mem == SLBM_MEM_HOST ? (double *)p->d_red : out;
+    const size_t bytes = (size_t)p->capacity * 7 * sizeof(double);
+    e = cudaMemsetAsync(dev_out, 0, bytes, p->stream);
+    for (int32_t s = 0; s < p->capacity && e == cudaSuccess; ++s) {
+        slbm_t *h = p->members[s];
+        if (h) e = launch_reduce_ext(h->d, dev_out + 7 * s, p->stream);
+    }
+    int32_t status = 0;
+    if (e == cudaSuccess && mem == SLBM_MEM_HOST) {
+        e = cudaMemcpyAsync(out, dev_out, bytes, cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    }
+    if (e != cudaSuccess) return pcuda(e, "pool reduce ext");
+    if (status == SLBM_EABORTED) return perr(SLBM_EABORTED, "a pool launch was aborted by the host flag");
+    set_error(SLBM_OK, "");
+    return SLBM_OK;
+}
+
 slbm_status slbm_pool_set_launch(slbm_pool_t *p, int32_t threads, int32_t ctas_per_sm) {
     if (!p) return perr(SLBM_EINVAL, "null pool");
     if (threads < 32 || threads > 128 || threads % 32) return perr(SLBM_EINVAL, "threads must be 32..128, multiple of 32");
@@ -922,6 +964,12 @@ void slbm_pool_free(slbm_pool_t *p) {
     free_aux(p);
     if (p->fork) cudaEventDestroy(p->fork);
     drop_pool_graphs(p);
+    for (slbm_t *h : p->members) {          // the members stay valid; they leave the pool
+        if (!h) continue;
+        std::vector<slbm_pool *> &ps = h->d.pools;
+        auto it = std::find(ps.begin(), ps.end(), p);
+        if (it != ps.end()) ps.erase(it);
+    }
     if (p->d_tab) cudaFree(p->d_tab);
     if (p->d_hdr) cudaFree(p->d_hdr);
     if (p->d_status) cudaFree(p->d_status);

@@ -208,6 +208,28 @@ class Domain:
     def reduce_device(self, out):
         A.check(A.lib().sparse_lbm_reduce(self.h, out.data_ptr(), A.MEM_DEVICE))
 
+    def reduce_ext(self, check: bool = True) -> np.ndarray:
+        """The five FP64 sums plus max |f_i - w_i| (unscaled) and max |u|.
+        check=False returns the values even when one is not finite or the
+        largest speed exceeds 0.3 (the library then reports EDIVERGED)."""
+        out = np.zeros(7)
+        st = A.lib().sparse_lbm_reduce_ext(self.h, out.ctypes.data, A.MEM_HOST)
+        if st != A.OK and (check or st != A.EDIVERGED):
+            A.check(st)
+        return out
+
+    def reduce_ext_device(self, out):
+        A.check(A.lib().sparse_lbm_reduce_ext(self.h, out.data_ptr(), A.MEM_DEVICE))
+
+    def set_storage(self, storage: int, scale_exp: int = 0):
+        """Convert the stored populations to another storage format or
+        power-of-two scale in place (exact for FP16/BF16 -> FP32 and for
+        rescales; FP32 -> FP16/BF16 rounds to nearest).  The domain must not
+        be a pool member."""
+        A.check(A.lib().sparse_lbm_set_storage(self.h, int(storage), int(scale_exp)))
+        inf = self.info
+        self.params["storage"], self.params["scale_exp"] = inf["storage"], inf["scale_exp"]
+
     def permeability(self, sums: np.ndarray | None = None) -> float:
         """Darcy permeability nu * U_D / F_x, U_D = sum u_x / N (lattice units^2)."""
         s = self.reduce() if sums is None else sums

@@ -65,6 +65,16 @@ class Pool:
     def reduce_device(self, out):
         A.check(A.lib().slbm_pool_reduce(self.h, out.data_ptr(), A.MEM_DEVICE))
 
+    def reduce_ext(self) -> np.ndarray:
+        """(capacity, 7): the five sums plus max |f_i - w_i| and max |u| per
+        slot; zeros for free slots."""
+        out = np.zeros((self.capacity, 7))
+        A.check(A.lib().slbm_pool_reduce_ext(self.h, out.ctypes.data, A.MEM_HOST))
+        return out
+
+    def reduce_ext_device(self, out):
+        A.check(A.lib().slbm_pool_reduce_ext(self.h, out.data_ptr(), A.MEM_DEVICE))
+
     def set_launch(self, threads: int, ctas_per_sm: int = 0):
         A.check(A.lib().slbm_pool_set_launch(self.h, int(threads), int(ctas_per_sm)))
 

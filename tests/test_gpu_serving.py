@@ -1,7 +1,8 @@
 """Continuous batching on the GPU: every served result equals the same request
-solved alone (bit for bit: same kernels, deterministic sums), FP16 storage
-stays within the permeability tolerance of FP32, and the FP32 permeability
-matches the FP64 oracle run for the same number of steps."""
+solved alone (bit for bit: same kernels, deterministic sums, storage changes
+at the same steps), FP16 and BF16 storage with the FP32 hand-off stay within
+the 1e-3 permeability target of FP32, and the FP32 permeability matches the
+FP64 oracle run for the same number of steps."""
 import numpy as np
 import pytest
 
@@ -10,7 +11,7 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 P = pytest.importorskip("paper_2408_06880_gb300")
-from paper_2408_06880_gb300.serving import GpuExecutor, Request, Server, solve_alone  # noqa: E402
+from paper_2408_06880_gb300.serving import GpuExecutor, Precision, Request, Server, solve_alone  # noqa: E402
 
 
 def small_requests(n=6, tol=1e-5, max_steps=6000):
@@ -24,13 +25,17 @@ def small_requests(n=6, tol=1e-5, max_steps=6000):
 
 
 @pytest.mark.parametrize("lanes", [None, ((20000, 3), (None, 1))])
-@pytest.mark.parametrize("storage", [P.FP32, P.FP16])
-def test_served_results_equal_alone(storage, lanes):
+@pytest.mark.parametrize("storage,plan", [(P.FP32, False), (P.FP16, False), (P.FP16, True), (P.BF16, True)])
+def test_served_results_equal_alone(storage, plan, lanes):
     # lanes: requests under 20000 cells (the 24^3 and 32^3 samples) advance
-    # three chunks per tick in their own pool, the others one
+    # three chunks per tick in their own pool, the others one.  plan: 16-bit
+    # storage handed off to FP32 (and rescaled) at the end of a tick, in the
+    # server and in the solve alone alike
     reqs = small_requests()
-    alone = {r.rid: solve_alone(r, storage=storage, scale_exp=24) for r in reqs}
-    ex = GpuExecutor(19, storage, capacity=3, scale_exp=24, lanes=lanes)     # fewer slots than requests
+    prec = Precision() if plan else None
+    ex = GpuExecutor(19, storage, capacity=3, scale_exp=24, lanes=lanes, precision=prec)   # fewer slots than requests
+    alone = {r.rid: solve_alone(r, storage=storage, scale_exp=24, precision=prec, tick=ex.tick_chunks(r))
+             for r in reqs}
     try:
         res, st = Server(ex, budget_bytes=1 << 34, chunk=100).run(reqs, realtime=False)
     finally:
@@ -39,25 +44,27 @@ def test_served_results_equal_alone(storage, lanes):
     for r in res:
         a = alone[r.rid]
         assert r.error is None
-        assert r.steps == a.steps and r.converged == a.converged
+        assert r.steps == a.steps and r.converged == a.converged and r.low_steps == a.low_steps
         assert r.permeability == a.permeability          # bit for bit
+        if plan:
+            assert 0 < r.low_steps < r.steps             # 16-bit phase, then FP32
     assert any(r.converged for r in res)
 
 
-def test_fp16_permeability_close_to_fp32():
-    # FP16 keeps 11 significant bits per stored population (relative rounding
-    # 2^-12 per store).  On these small, strongly forced samples the measured
-    # permeability error against FP32 was 1.3e-5 .. 1.5e-3; the bound below is
-    # that of this test case, the stream workload's error is reported by
-    # bench.py --mode serve.
+@pytest.mark.parametrize("storage", [P.FP16, P.BF16])
+def test_low_precision_permeability_within_target_of_fp32(storage):
+    # With the hand-off the solve ends in FP32 at the request's tolerance, so
+    # the 16-bit storage changes the result by far less than the 1e-3 target.
+    # (Without it, FP16 solves of these samples stall 1.3e-5 .. 1.5e-3 away
+    # from the FP32 permeability, and BF16 ones further.)
     reqs = small_requests(4, tol=1e-6, max_steps=8000)
     errs = []
     for r in reqs:
-        k32 = solve_alone(r, storage=P.FP32).permeability
-        k16 = solve_alone(r, storage=P.FP16, scale_exp=24).permeability
-        errs.append(abs(k16 / k32 - 1))
-    assert max(errs) <= 3e-3, errs
-    assert float(np.median(errs)) <= 5e-4, errs
+        k32 = solve_alone(r, storage=P.FP32)
+        k16 = solve_alone(r, storage=storage, scale_exp=24, precision=Precision())
+        assert k32.converged and k16.converged and 0 < k16.low_steps < k16.steps
+        errs.append(abs(k16.permeability / k32.permeability - 1))
+    assert max(errs) <= 1e-3, errs
 
 
 def test_fp32_permeability_matches_oracle():

@@ -271,3 +271,117 @@ def test_lane_cap_bounds_concurrent_large_requests():
     res, st = Server(ex, 10 ** 9).run(reqs, realtime=False)
     assert st["solved"] == 8
     assert ex.peak_large == 2
+
+
+# ------------------------------------------------------ reduced precision
+from paper_2408_06880_gb300.serving import Precision, Track  # noqa: E402
+
+
+class FakeMixedExecutor(FakeExecutor):
+    """16-bit requests relax like FP32 ones until the relative error of the
+    mean velocity reaches `floor`, where they stall (the rounding of small
+    changes); after a conversion to FP32 they relax to the steady state from
+    where they stood.  Sums carry the two maxima of reduce_ext (max|g| grows
+    with the velocity; max|u| is 10 x the mean)."""
+
+    def __init__(self, capacity=4, floor=2e-3, gscale=0.05, chunks=None):
+        super().__init__(capacity)
+        self.storage, self.scale_exp, self.precision = A.FP16, 24, Precision()
+        self.floor, self.gscale = floor, gscale
+        self.converted = []          # (rid, step, storage, scale)
+        self.chunks = chunks
+        if chunks is not None:
+            self.launch, self.collect = self._launch, self._collect
+
+    def open(self, req):
+        d = super().open(req)
+        d.storage, d.scale, d.t16, d.m0 = A.FP16, 24, None, 0.0
+        return d
+
+    def _mean(self, d):
+        U = 1e-3
+        T = d.req.meta.get("T", 500.0)
+        if d.storage != A.FP32:
+            return U * (1 - max(math.exp(-d.t / T), self.floor))
+        return U - (U - d.m0) * math.exp(-(d.t - d.t16) / T)
+
+    def _row(self, d):
+        m = self._mean(d)
+        return np.array([0, 0, 0, 0, m * d.nf, self.gscale * m, 10 * m])
+
+    def sums(self):
+        out = np.zeros((self.capacity, 7))
+        for s, d in self.slots.items():
+            out[s] = self._row(d)
+        return out
+
+    def _launch(self, k):
+        self.series = {}
+        for s, d in self.slots.items():
+            rows = []
+            for _ in range(self.chunks):
+                d.t += k
+                rows.append(self._row(d))
+            self.series[s] = np.array(rows)
+
+    def _collect(self):
+        return self.series
+
+    def convert(self, slot, dom, storage, scale):
+        if storage == A.FP32 and dom.storage != A.FP32:
+            dom.m0, dom.t16 = self._mean(dom), dom.t
+        dom.storage, dom.scale = storage, scale
+        self.converted.append((dom.req.rid, dom.t, storage, scale))
+        return slot
+
+
+def test_precision_plan_hands_off_to_fp32_and_converges():
+    ex = FakeMixedExecutor(capacity=3)
+    reqs = [req(i, T=300.0 + 100 * i) for i in range(5)]
+    res, st = Server(ex, budget_bytes=10 ** 9, chunk=100).run(reqs, realtime=False)
+    assert st["solved"] == 5 and st["converged"] == 5
+    handoffs = {rid: t for rid, t, s, _ in ex.converted if s == A.FP32}
+    for r in res:
+        assert r.rid in handoffs
+        assert 0 < r.low_steps == handoffs[r.rid] < r.steps       # 16-bit phase first, then FP32
+        assert abs(r.mean_ux / 1e-3 - 1) < 1e-4                   # converged in FP32, past the 16-bit floor
+    assert 0 < st["low_precision_step_share"] < 1
+
+
+def test_precision_changes_take_effect_at_tick_ends():
+    ex = FakeMixedExecutor(capacity=4, chunks=3)
+    reqs = [req(i, T=400.0 + 50 * i) for i in range(4)]
+    res, st = Server(ex, budget_bytes=10 ** 9, chunk=100).run(reqs, realtime=False)
+    assert st["solved"] == 4
+    for rid, t, storage, _ in ex.converted:
+        assert t % 300 == 0                        # after whole ticks of 3 chunks of 100 steps
+
+
+def test_rescale_keeps_the_stored_maximum_in_band():
+    p = Precision()
+    assert p.rescale_to(24, 1e-4) is None                       # 1e-4 * 2^24 = 1678: inside [2^10, 2^14.5]
+    s = p.rescale_to(24, 2e-3)                                  # 33554 > 2^14.5
+    assert s is not None and 2 ** 12 < 2e-3 * 2.0 ** s <= 2 ** 13
+    s = p.rescale_to(24, 1e-6)                                  # 16.8 < 2^10
+    assert s is not None and 2 ** 12 < 1e-6 * 2.0 ** s <= 2 ** 13
+    assert p.rescale_to(24, float("nan")) is None and p.rescale_to(24, 0.0) is None
+    assert p.rescale_to(0, 1e30) == -40                         # clamped to the format's exponent range
+
+
+def test_track_rescale_pending_and_handoff_override():
+    r = req(0)
+    tr = Track(r, r.n_fluid, A.FP16, 24, Precision())
+    nf = r.n_fluid
+    tr.check(np.array([0, 0, 0, 0, 1e-4 * nf, 5e-3, 1e-3]), 100)        # max|h| = 5e-3 * 2^24 > 2^14.5
+    assert tr.pending is not None and tr.pending[0] == A.FP16 and tr.pending[1] < 24
+    tr.check(np.array([0, 0, 0, 0, 1.00001e-4 * nf, 5e-3, 1e-3]), 100)  # rel change 1e-5 < 3e-3
+    assert tr.pending == (A.FP32, 0)
+    tr.switched()
+    assert tr.storage == A.FP32 and tr.precision is None and tr.low_steps == 200
+
+
+def test_track_divergence_from_the_largest_speed():
+    r = req(0)
+    tr = Track(r, r.n_fluid)
+    done, err, conv = tr.check(np.array([0, 0, 0, 0, 1e-4 * r.n_fluid, 1e-3, 0.31]), 100)
+    assert done and "speed" in err and not conv
