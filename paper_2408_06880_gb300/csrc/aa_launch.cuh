@@ -5,6 +5,7 @@
 #include <tuple>
 
 #include "aa_kernels.cuh"
+#include "aa_window.cuh"
 #include "internal.h"
 
 namespace slbm {
@@ -62,6 +63,43 @@ static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
         }
     }
     return cudaGetLastError();
+}
+
+// Odd step from bulk-staged tiles and neighbour windows (launch variant 6),
+// NSTAGE stages in dynamic shared memory.
+template <int Q, int ST, bool BC, int NSTAGE>
+static cudaError_t launch_window_n(const Domain &d, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    auto k = aa_odd_window_kernel<Q, ST, BC, NSTAGE>;
+    const size_t smem = window_smem_bytes<Q, ST>(NSTAGE);
+    {   // the dynamic shared memory above 48 KB, set once per device before the occupancy query
+        static std::mutex mu;
+        static std::map<int, bool> done;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done[dev]) {
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
+    const int32_t S = (int32_t)d.S;
+    k<<<persistent_grid(k, WIN_TILE + 32, S / WIN_TILE, smem), WIN_TILE + 32, smem, st>>>(
+        reinterpret_cast<T *>(d.pdf.p), reinterpret_cast<const int32_t *>(d.P.p), S, (int32_t)d.n_fluid,
+        reinterpret_cast<const WinSpan *>(d.win_tab.p), reinterpret_cast<const LinkMap *>(d.link_map.p),
+        d.collide_params(), reinterpret_cast<int32_t *>(d.err.p));
+    return cudaGetLastError();
+}
+
+template <int Q, int ST, bool BC>
+static cudaError_t launch_window(const Domain &d, int nstage, cudaStream_t st) {
+    switch (nstage) {
+        case 2: return launch_window_n<Q, ST, BC, 2>(d, st);
+        case 3: return launch_window_n<Q, ST, BC, 3>(d, st);
+        case 4: return launch_window_n<Q, ST, BC, 4>(d, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Boundary fix-up launches around the even step of a domain with links.
@@ -220,6 +258,12 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
         const int32_t pfc = (int32_t)persistent_grid(kc, sh.threads, INT32_MAX);
         kc<<<grid(sh.cells), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfc, code, cb);
         return cudaGetLastError();
+    }
+    // variant 6: every read of a tile staged in shared memory (index rows, own
+    // rows, neighbour windows) by the bulk-copy engine, `cells` stages
+    if (sh.variant == 6) {
+        if (!d.win_tab.p) return cudaErrorInvalidValue;
+        return bc ? launch_window<Q, ST, true>(d, sh.cells, st) : launch_window<Q, ST, false>(d, sh.cells, st);
     }
     // variant 5: variant 2 held to 64 registers a thread (more resident warps)
     if (sh.variant == 5) {

@@ -175,7 +175,7 @@ static void drop_graphs(Domain &d) {
 
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
-    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.cell_voxel, &d.link_cell,
+    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.cell_voxel, &d.link_cell,
                       &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask,
                       &d.red_partial, &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
@@ -200,6 +200,19 @@ static slbm_status ensure_codes(Domain &d) {
     if (build_link_codes(cx, d) || cx.check(cudaStreamSynchronize(d.stream), "build codes")) {
         cx.release(d.code);
         cx.release(d.code_base);
+        return cx.status == SLBM_OK ? err(SLBM_ECUDA, g_msg) : cx.status;
+    }
+    return SLBM_OK;
+}
+
+// Build the neighbour-window table of the staged odd step on first use
+// (sparse layout only).
+static slbm_status ensure_window(Domain &d) {
+    if (d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "the staged odd step exists for the sparse layout only");
+    if (d.win_tab.p || d.S == 0) return SLBM_OK;
+    Ctx cx = d.ctx();
+    if (build_window_tab(cx, d) || cx.check(cudaStreamSynchronize(d.stream), "build window table")) {
+        cx.release(d.win_tab);
         return cx.status == SLBM_OK ? err(SLBM_ECUDA, g_msg) : cx.status;
     }
     return SLBM_OK;
@@ -639,6 +652,12 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             return err(SLBM_EUNSUPPORTED, "the staged variants cover sparse FP32/FP16 domains");
         if ((threads != 64 && threads != 128) || (cells != 2 && cells != 4))
             return err(SLBM_EINVAL, "staged variant: tile 64 or 128, stages 2 or 4");
+    } else if (parity == 1 && variant == 6) {
+        if (h->d.layout != SLBM_LAYOUT_SPARSE) return err(SLBM_EUNSUPPORTED, "the staged odd step covers sparse domains");
+        if (threads != 128 || cells < 2 || cells > 4)
+            return err(SLBM_EINVAL, "odd variant 6: 128 threads (one tile of cells), 2..4 stages");
+        const slbm_status st = ensure_window(h->d);
+        if (st != SLBM_OK) return st;
     } else if (parity == 1 && variant >= 2 && variant <= 5) {
         if (threads < 32 || threads > 256 || threads % 32 || (cells != 1 && !((variant == 2 || variant == 4) && cells == 2)))
             return err(SLBM_EINVAL, "odd variants 2..5: threads 32..256 (multiple of 32), "
@@ -648,7 +667,7 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
             if (st != SLBM_OK) return st;
         }
     } else {
-        return err(SLBM_EINVAL, "variant must be 0..3 (even step) or 0..5 (odd step)");
+        return err(SLBM_EINVAL, "variant must be 0..3 (even step) or 0..6 (odd step)");
     }
     h->d.shape[parity] = LaunchShape{threads, cells, variant};
     drop_graphs(h->d);

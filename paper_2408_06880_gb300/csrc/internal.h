@@ -71,6 +71,7 @@ struct Domain {
     DevBuf P;                          // (Q-1) x S odd-step slots R(i,k) (row-flipped pull entries)
     DevBuf code;                       // (Q-1) x S 16-bit link codes of R (sparse)
     DevBuf code_base;                  // (S / CODE_TILE) x (Q-1) column bases of the codes
+    DevBuf win_tab;                    // (S / 128) x (Q-1) neighbour windows of the staged odd step
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity
@@ -115,6 +116,8 @@ constexpr int RED_CHUNK = RED_THREADS * RED_CELLS_PER_THREAD;
 cudaError_t launch_unflip(const Domain &d, int32_t *out, cudaStream_t st);
 // 16-bit link codes of the odd-step slots (after build_sparse_lists)
 int build_link_codes(Ctx &cx, Domain &d);
+// neighbour-window table of the staged odd step (launch variant 6)
+int build_window_tab(Ctx &cx, Domain &d);
 int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, const float *h_inlet_u,
                        int64_t n_inlet_u);
 // aa_q19.cu / aa_q27.cu (dispatch in api.cu)

@@ -5,6 +5,7 @@
 // The compaction is an exclusive prefix sum of (flag == fluid) over voxel ids,
 // so cell k is the k-th fluid voxel in ascending id: exactly the order of a
 // sequential scan, whatever the launch shape (integer sums are exact).
+#include "aa_window.cuh"
 #include "internal.h"
 
 namespace slbm {
@@ -509,6 +510,20 @@ int build_link_codes(Ctx &cx, Domain &d) {
         build_codes_kernel<27><<<(unsigned)tiles, CODE_TILE, 0, cx.stream>>>(
             (const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid, (uint16_t *)d.code.p, (int32_t *)d.code_base.p);
     return cx.check(cudaGetLastError(), "build_codes launch");
+}
+
+int build_window_tab(Ctx &cx, Domain &d) {
+    if (d.S == 0) return 0;
+    const int64_t n = d.S / WIN_TILE * (d.q - 1);
+    if (cx.alloc(d.win_tab, n * (int64_t)sizeof(WinSpan))) return -1;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (d.q == 19)
+        build_window_table<19><<<grid, 128, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid,
+                                                             (WinSpan *)d.win_tab.p);
+    else
+        build_window_table<27><<<grid, 128, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid,
+                                                             (WinSpan *)d.win_tab.p);
+    return cx.check(cudaGetLastError(), "build_window_table launch");
 }
 
 }  // namespace slbm

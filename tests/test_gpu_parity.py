@@ -158,7 +158,8 @@ def test_reductions_match_fields_and_are_deterministic():
 
 SHAPES = [(64, 1, 0), (128, 1, 0), (256, 1, 0), (64, 2, 0), (256, 2, 0), (128, 4, 0), (256, 4, 0),
           (64, 2, 1), (64, 4, 1), (128, 2, 1), (128, 4, 1), (64, 1, 2), (128, 1, 2), (128, 1, 3), (64, 1, 3), (128, 2, 2),
-          (128, 1, 4), (64, 1, 4), (128, 2, 4), (256, 2, 4), (128, 1, 5), (256, 1, 5), (64, 1, 5)]
+          (128, 1, 4), (64, 1, 4), (128, 2, 4), (256, 2, 4), (128, 1, 5), (256, 1, 5), (64, 1, 5),
+          (128, 2, 6), (128, 3, 6), (128, 4, 6)]
 
 
 @pytest.mark.parametrize("storage", [P.FP32, P.FP16])
@@ -183,6 +184,51 @@ def test_launch_shapes_are_bitwise_identical(shape, q, storage):
         got, _ = d.get_state()
         assert d.device_error() == 0
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("case", ["sweep96_lex", "sweep96_brick", "dense96", "bed_links", "bf16"])
+def test_window_staged_odd_step_over_many_tiles(case, stages):
+    # odd variant 6 (index rows, own rows and neighbour windows bulk-copied
+    # into a ring of shared-memory stages) on domains with many more 128-cell
+    # tiles than resident CTAs, so every CTA cycles through its ring; brick-8
+    # order and the near-all-fluid packing send more links outside the
+    # windows (read from global memory); the bed carries inlet/outlet links
+    q, storage, order = 19, P.FP32, P.ORDER_LEX
+    if case == "sweep96_lex":
+        g = G.boolean_spheres(96, 0.5, 9)
+    elif case == "sweep96_brick":
+        g, order, storage = G.boolean_spheres(96, 0.5, 9), P.ORDER_BRICK8, P.FP16
+    elif case == "dense96":
+        g, storage = G.boolean_spheres(96, 0.9, 14), P.FP16
+    elif case == "bf16":
+        g, storage = G.boolean_spheres(80, 0.7, 4), P.BF16
+    else:
+        g, q = G.particle_bed(96, 64, 64, bed_top=32, radius=5.0, seed=23), 27
+    kw = dict(q=q, op=P.TRT, force=(1e-5, 2e-6, 0.0), storage=storage, scale_exp=20, cell_order=order)
+    with gpu_domain(g, **kw) as ref:
+        ref.step(9)
+        want, _ = ref.get_state()
+    with gpu_domain(g, **kw) as d:
+        d.set_launch(1, 128, stages, 6)
+        assert d.n_fluid > 400 * 128                   # many tiles per CTA
+        d.step(9)
+        got, _ = d.get_state()
+        assert d.device_error() == 0
+    assert np.array_equal(got, want)
+
+
+def test_window_staged_shape_refusals():
+    g = G.boolean_spheres(16, 0.5, 2)
+    with gpu_domain(g, q=19, op=P.TRT) as d:
+        for bad in ((64, 2, 6), (128, 1, 6), (128, 5, 6)):
+            with pytest.raises(P.SlbmError):
+                d.set_launch(1, *bad)
+        with pytest.raises(P.SlbmError):
+            d.set_launch(0, 128, 2, 6)                  # odd step only
+    with gpu_domain(g, q=19, op=P.TRT, layout=P.SPARSE_PULL) as d:
+        with pytest.raises(P.SlbmError):
+            d.set_launch(1, 128, 2, 6)
 
 
 EVEN_PAIRED = [(64, 2, 2), (128, 2, 2), (256, 2, 2), (64, 4, 2), (256, 4, 2), (64, 2, 3), (64, 4, 3), (128, 2, 3),
