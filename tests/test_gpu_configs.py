@@ -64,6 +64,38 @@ def test_sweep_full_size(phi, seed):
     assert_fields_close(rho, u, rho_o, u_o)
 
 
+def _fixture(name):
+    import os
+    return np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name))
+
+
+def _assert_sampled(fx, rho, u, sums, u_tol=U_TOL):
+    # (rho, u) of the oracle's sampled cells, and its five domain sums over all
+    # cells (written by tests/golden/make_oracle_fixtures.py from the oracle)
+    c = fx["cells"]
+    assert rel_l2(u[c], fx["u"]) <= u_tol, rel_l2(u[c], fx["u"])
+    assert np.max(np.abs(rho[c] - fx["rho"])) <= 1e-6
+    o = fx["sums"]
+    assert abs(sums[0] - o[0]) <= 1e-6 * int(fx["n_fluid"]) ** 0.5     # mass: FP32 rounding only
+    for j in (1, 4):                                                  # x momentum and sum of u_x
+        assert abs(sums[j] / o[j] - 1) <= u_tol, (j, sums[j], o[j])
+
+
+def test_sweep_full_size_full_step_count():
+    # the 256^3 porosity-0.5 domain of the benchmark, default launch shapes,
+    # the full 1000 TRT steps, against the FP64 oracle's sparse stepper on the
+    # same domain (its fields at 32768 sampled cells and its domain sums,
+    # stored in tests/golden/sweep256_phi05_trt_1000.npz)
+    fx = _fixture("sweep256_phi05_trt_1000.npz")
+    g = G.boolean_spheres(256, 0.5, 12)
+    with gpu_domain(g, q=19, force=(1e-6, 0.0, 0.0), **TRT) as d:
+        assert d.n_fluid == int(fx["n_fluid"])
+        d.step(1000)
+        rho, u = d.macroscopic(P.ORDER_CELLS)
+        sums = d.reduce()
+    _assert_sampled(fx, rho.astype(np.float64), u.T.astype(np.float64), sums)
+
+
 def test_sweep_scaled_full_step_count():
     g = G.boolean_spheres(64, 0.5, 12)
     force = (1e-6, 0.0, 0.0)
@@ -94,6 +126,26 @@ def test_bed_full_size():
     assert lists["link_cell"].size > 0
     assert_lists_equal(lists, L)
     assert_fields_close(rho, u, rho_o, u_o)
+
+
+def test_bed_full_size_200_steps():
+    # the full 512 x 256 x 256 particle bed (D3Q27 TRT, velocity inlet 0.05,
+    # pressure outlet), default launch shapes, 200 steps, against the oracle's
+    # stored fields (tests/golden/bed_full_q27_200.npz)
+    fx = _fixture("bed_full_q27_200.npz")
+    g = G.particle_bed()
+    with gpu_domain(g, q=27, force=(0.0, 0.0, 0.0), **TRT) as d:
+        assert d.n_fluid == int(fx["n_fluid"])
+        d.step(200)
+        rho, u = d.macroscopic(P.ORDER_CELLS)
+        sums = d.reduce()
+    c = fx["cells"]
+    u = u.T.astype(np.float64)
+    assert rel_l2(u[c], fx["u"]) <= U_TOL, rel_l2(u[c], fx["u"])
+    assert np.max(np.abs(rho[c] - fx["rho"])) <= 1e-6
+    o = fx["sums"]
+    for j in (0, 1, 4):                   # mass (the inlet adds it), x momentum, sum of u_x
+        assert abs(sums[j] / o[j] - 1) <= U_TOL, (j, sums[j], o[j])
 
 
 def test_bed_scaled_full_step_count_fp32_and_fp16():

@@ -75,3 +75,27 @@ def test_fp32_permeability_matches_oracle():
     f = O.dense_run(p, O.dense_init(p), r.steps)
     k_oracle = O.permeability(p, O.reductions(p, f)[4])
     assert abs(r.permeability / k_oracle - 1) <= 1e-5
+
+
+def test_stream_subset_fp16_with_handoff_vs_oracle():
+    # the first 16 requests of edge 64 or 96 of the permeability stream,
+    # FP16 storage with the FP32 hand-off, each solved to the 1e-6 criterion,
+    # against the FP64 oracle's permeability at the same step count (the
+    # oracle's sum of u_x every 100 steps, tests/golden/serving16_oracle.json,
+    # written by tests/golden/make_oracle_fixtures.py)
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "serving16_oracle.json")
+    with open(path) as f:
+        ref = json.load(f)
+    assert len(ref["requests"]) == 16
+    errs = []
+    for o in ref["requests"]:
+        g = G.serving_request(o["rid"])
+        req = Request(o["rid"], g.flags, force=(1e-6, 0.0, 0.0), max_steps=20000, tol=1e-6)
+        r = solve_alone(req, storage=P.FP16, precision=Precision())
+        assert r.converged and 0 < r.low_steps < r.steps
+        j = min(r.steps // 100, len(o["sum_ux"])) - 1
+        k_o = o["nu"] * (o["sum_ux"][j] / o["n_voxels"]) / 1e-6
+        errs.append(abs(r.permeability / k_o - 1))
+    assert max(errs) <= 1e-3, errs

@@ -212,3 +212,31 @@ def test_host_list_validator_accepts_valid_and_rejects_planted_mistakes():
         if L.n_fluid < S:
             with pytest.raises(ValueError):
                 validate_pull_list(bad, L.n_fluid, nl)
+
+
+# ------------------------------------------- stored oracle values (tests/golden)
+def test_stored_oracle_fixtures_match_their_recipes():
+    # the fixtures the long GPU parity tests compare with were written by
+    # tests/golden/make_oracle_fixtures.py from the oracle: their sizes and
+    # seeded cell samples follow the recipe, and the first chunk of a stored
+    # serving trajectory is what the oracle computes now
+    import json
+    import os
+    import geometry as G
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    for name, nf in (("sweep256_phi05_trt_1000.npz", 8388390), ("bed_full_q27_200.npz", 23121575)):
+        fx = np.load(os.path.join(here, name))
+        assert int(fx["n_fluid"]) == nf
+        want = np.sort(np.random.default_rng(2408).choice(nf, size=32768, replace=False))
+        assert np.array_equal(fx["cells"], want)
+        assert fx["u"].shape == (32768, 3) and np.all(np.isfinite(fx["u"]))
+    with open(os.path.join(here, "serving16_oracle.json")) as f:
+        ref = json.load(f)
+    assert [r["rid"] for r in ref["requests"]] == [2, 3, 7, 8, 10, 12, 14, 15, 16, 20, 21, 25, 26, 29, 31, 34]
+    o = next(r for r in ref["requests"] if r["rid"] == 26)         # the smallest request
+    g = G.serving_request(26)
+    p = O.Problem.from_geometry(g, q=19, op=O.TRT, omega_plus=1.25, magic=3 / 16, force=(1e-6, 0.0, 0.0))
+    L = O.pull_list(p)
+    f = O.sparse_run(p, L, O.sparse_rest(p, L), 100)
+    _, u = O.sparse_macroscopic(p, L, f)
+    assert float(np.sum(u[:, 0])) == o["sum_ux"][0]
