@@ -87,7 +87,8 @@ static cudaError_t launch_window_n(const Domain &d, cudaStream_t st) {
     const int32_t S = (int32_t)d.S;
     k<<<persistent_grid(k, WIN_TILE + 32, S / WIN_TILE, smem), WIN_TILE + 32, smem, st>>>(
         reinterpret_cast<T *>(d.pdf.p), reinterpret_cast<const int32_t *>(d.P.p), S, (int32_t)d.n_fluid,
-        reinterpret_cast<const WinSpan *>(d.win_tab.p), reinterpret_cast<const LinkMap *>(d.link_map.p),
+        reinterpret_cast<const WinSpan *>(d.win_tab.p), reinterpret_cast<const uint16_t *>(d.win_code.p),
+        reinterpret_cast<const LinkMap *>(d.link_map.p),
         d.collide_params(), reinterpret_cast<int32_t *>(d.err.p));
     return cudaGetLastError();
 }

@@ -16,11 +16,19 @@
 //     neighbour's slot (a neighbour across a periodic wrap falls outside and
 //     is read from global memory).
 // A per-tile table (built once per domain, `build_window_table`) gives each
-// window's first column and length; it is copied in with the tile.  One warp
-// issues the copies of tile t + NSTAGE*grid into a ring of NSTAGE stages
-// while the CTA computes tile t from shared memory, so the copy engine keeps
-// the DRAM reads in flight and the threads only compute and scatter.  The
-// scatter to R(inverse-direction slot) stays a plain store per population.
+// window's first column and length; it is copied in with the tile.  Instead
+// of the tile's int32 index rows, the stage holds 16-bit window codes (built
+// with the table, `build_window_codes`): per link, the position of the slot
+// R(i,k) among the stage's staged populations (own rows, then windows), or an
+// escape value for a fluid neighbour outside its window and for a boundary
+// link, which read the int32 slot list instead.  A cell then gathers with one
+// shared-memory load per link, recovers R(i,k) for the scatter from the code
+// and its window's first column, and the odd step reads 2 index bytes per
+// link instead of 4.  One warp issues the copies of tile t + NSTAGE*grid
+// into a ring of NSTAGE stages while the other warps compute tile t from
+// shared memory, so the copy engine keeps the DRAM reads in flight and the
+// computing threads only compute and scatter.  The scatter to the slots read
+// stays a plain store per population.
 //
 // Reading the windows in place is race-free: each slot is read and written
 // by one cell only (the AA odd step writes back to the slots it read), so
@@ -34,32 +42,49 @@ namespace slbm {
 
 constexpr int WIN_TILE = 128;                 // cells per tile (= threads per CTA)
 constexpr int WIN_MARGIN = 16;                // cells of slack on each side of a window
-constexpr int WIN_CELLS = WIN_TILE + 2 * WIN_MARGIN + 8;   // window capacity (alignment included)
+constexpr int WIN_CELLS = WIN_TILE + 2 * WIN_MARGIN + 8;   // main window capacity (alignment included)
+constexpr int WIN2_CELLS = 24;                // secondary window capacity
 
-// Table entry of one tile and direction: first column of the window in row
-// inverse(i) (a multiple of 8) and its length in cells (a multiple of 8,
-// 0 = no window: no fluid neighbour in that direction).
+// Table entry of one tile and direction: the main window (first column in
+// row inverse(i), a multiple of 8, and length in cells, a multiple of 8; 0 =
+// no fluid neighbour in that direction) and a short secondary window for the
+// fluid neighbours the main one misses -- with lexicographic numbering these
+// are the pull neighbours across the periodic x wrap, at the far end of the
+// same row (0 = none, or they do not fit).
 struct WinSpan {
-    int32_t first, len;
+    int32_t first, len, first2, len2;
 };
 
-// Byte layout of one stage of the ring, for Q directions and element type T.
+// Codes: bits 0-14 a position among the staged populations, bit 15 set for
+// a boundary link (gather from the own slot, scatter through the link map);
+// WIN_ESCAPE: a fluid neighbour outside both windows (read through the int32
+// slot list).
+constexpr uint32_t WIN_ESCAPE = 0xFFFF;
+constexpr uint32_t WIN_LINK = 0x8000;
+
+// Byte layout of one stage of the ring, for Q directions and element type T:
+// the codes, the staged populations (own rows [Q][TILE], main windows
+// [Q-1][WIN_CELLS], secondary windows [Q-1][WIN2_CELLS]) and the table.
 template <int Q, class T>
 struct WinStage {
     static constexpr int R1 = Q - 1;
-    static constexpr uint32_t IDX = 0;                                        // int32 [R1][TILE]
-    static constexpr uint32_t OWN = IDX + R1 * WIN_TILE * 4;                  // T [Q][TILE]
-    static constexpr uint32_t WIN = OWN + ((Q * WIN_TILE * sizeof(T) + 15) / 16) * 16;   // T [R1][WIN_CELLS]
-    static constexpr uint32_t TAB = WIN + ((R1 * WIN_CELLS * sizeof(T) + 15) / 16) * 16; // WinSpan [R1]
+    static constexpr uint32_t OWN_ELEMS = Q * WIN_TILE;                        // code < OWN_ELEMS: own slot
+    static constexpr uint32_t WIN2_ELEMS = OWN_ELEMS + R1 * WIN_CELLS;         // first secondary position
+    static constexpr uint32_t POP_ELEMS = WIN2_ELEMS + R1 * WIN2_CELLS;
+    static constexpr uint32_t CODE = 0;                                        // uint16 [R1][TILE]
+    static constexpr uint32_t POP = CODE + R1 * WIN_TILE * 2;                  // T [POP_ELEMS]
+    static constexpr uint32_t TAB = POP + ((POP_ELEMS * sizeof(T) + 15) / 16) * 16;
     static constexpr uint32_t BYTES = TAB + ((R1 * sizeof(WinSpan) + 15) / 16) * 16;
+    static_assert(POP_ELEMS < WIN_LINK, "positions fit in 15 bits");
 };
 
 // Window table of one domain: for tile t and direction i = r + 1, the fluid
 // neighbours' columns n (slot R(i,k) = inverse(i)*S + n) of the tile's cells.
-// The window is centred on the offset n - k of one of three reference cells
-// (the first, middle and last fluid-linked cell of the tile), whichever
-// covers most of the tile's links, with WIN_MARGIN cells of slack; it is
-// clipped to [0, S).  One thread per (tile, direction).
+// The main window is centred on the offset n - k of one of three reference
+// cells (the first, middle and last fluid-linked cell of the tile), whichever
+// covers most of the tile's links, with WIN_MARGIN cells of slack, clipped to
+// [0, S); the secondary one spans the remaining columns if they lie within
+// WIN2_CELLS of each other.  One thread per (tile, direction).
 template <int Q>
 __global__ void build_window_table(const int32_t *__restrict__ R, int32_t S, int32_t nf, WinSpan *__restrict__ tab) {
     const int32_t id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,7 +110,7 @@ __global__ void build_window_table(const int32_t *__restrict__ R, int32_t S, int
             mid = k;
         }
     }
-    WinSpan w{0, 0};
+    WinSpan w{0, 0, 0, 0};
     if (first >= 0) {
         const int32_t refs[3] = {first, mid, last};
         int32_t best = -1;
@@ -108,51 +133,105 @@ __global__ void build_window_table(const int32_t *__restrict__ R, int32_t S, int
             }
             if (cov > best) {
                 best = cov;
-                w = WinSpan{(int32_t)lo, (int32_t)len};
+                w.first = (int32_t)lo;
+                w.len = (int32_t)len;
+            }
+        }
+        // the columns the main window misses
+        int64_t lo2 = INT64_MAX, hi2 = -1;
+        for (int32_t k = k0; k < kend; ++k) {
+            const int64_t dk = offset_of(k);
+            if (dk == INT64_MIN) continue;
+            const int64_t n = k + dk;
+            if (n >= w.first && n < w.first + w.len) continue;
+            lo2 = n < lo2 ? n : lo2;
+            hi2 = n > hi2 ? n : hi2;
+        }
+        if (hi2 >= 0) {
+            lo2 = (lo2 / 8) * 8;
+            const int64_t len2 = ((hi2 + 1 - lo2 + 7) / 8) * 8;
+            if (len2 <= WIN2_CELLS && lo2 + len2 <= S) {
+                w.first2 = (int32_t)lo2;
+                w.len2 = (int32_t)len2;
             }
         }
     }
     tab[id] = w;
 }
 
+// Window codes of one domain (after the table): per direction i = r + 1 and
+// cell k, the position of the slot R(i,k) among the staged populations of
+// k's tile -- a fluid neighbour inside its main window: OWN_ELEMS +
+// r*WIN_CELLS + (n - first); inside its secondary window: WIN2_ELEMS +
+// r*WIN2_CELLS + (n - first2); a wall (R = i*S + k): i*TILE + k mod TILE; a
+// boundary link: the same own position with WIN_LINK set -- or WIN_ESCAPE (a
+// fluid neighbour outside both windows, padding).
+template <int Q>
+__global__ void build_window_codes(const int32_t *__restrict__ R, int32_t S, int32_t nf,
+                                   const WinSpan *__restrict__ tab, uint16_t *__restrict__ code) {
+    using L = WinStage<Q, float>;                      // positions do not depend on the element type
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (k >= S) return;
+    const int i = r + 1;
+    uint32_t c = WIN_ESCAPE;
+    if (k < nf) {
+        const int32_t e = R[(int64_t)r * S + k];
+        const int32_t row_b = inv(i) * S;
+        if (e < 0) {
+            c = (i * WIN_TILE + k % WIN_TILE) | WIN_LINK;
+        } else if (e - row_b >= 0 && e - row_b < S) {
+            const WinSpan w = tab[(int64_t)(k / WIN_TILE) * (Q - 1) + r];
+            const int32_t n = e - row_b;
+            if (n >= w.first && n < w.first + w.len) c = L::OWN_ELEMS + r * WIN_CELLS + (n - w.first);
+            else if (n >= w.first2 && n < w.first2 + w.len2) c = L::WIN2_ELEMS + r * WIN2_CELLS + (n - w.first2);
+        } else if (e == i * S + k) {
+            c = i * WIN_TILE + k % WIN_TILE;
+        }
+    }
+    code[(int64_t)r * S + k] = (uint16_t)c;
+}
+
 // The odd step of one tile's cells from a filled stage.
 template <int Q, int ST, bool HAS_BC>
-__device__ __forceinline__ void window_cell(typename Store<ST>::T *__restrict__ pdf, const unsigned char *stage,
-                                            int tid, int32_t k, int32_t S, const LinkMap *__restrict__ maps,
-                                            const CollideParams &p) {
+__device__ __forceinline__ void window_cell(typename Store<ST>::T *__restrict__ pdf, const int32_t *__restrict__ R,
+                                            const unsigned char *stage, int tid, int32_t k, int32_t S,
+                                            const LinkMap *__restrict__ maps, const CollideParams &p) {
     using St = Store<ST>;
     using T = typename St::T;
     using L = WinStage<Q, T>;
-    const int32_t *idx = reinterpret_cast<const int32_t *>(stage + L::IDX);
-    const T *own = reinterpret_cast<const T *>(stage + L::OWN);
-    const T *win = reinterpret_cast<const T *>(stage + L::WIN);
+    const uint16_t *code = reinterpret_cast<const uint16_t *>(stage + L::CODE);
+    const T *pop = reinterpret_cast<const T *>(stage + L::POP);
     const WinSpan *tab = reinterpret_cast<const WinSpan *>(stage + L::TAB);
     float g[Q];
-    int32_t e[Q];
-    g[0] = St::raw(own[tid]);
+    int32_t slot[Q];
+    g[0] = St::raw(pop[tid]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int32_t ee = idx[(i - 1) * WIN_TILE + tid];
-        e[i] = ee;
-        // A slot inside the window is a fluid neighbour's (a wall's own slot
-        // lies in row i, a link's entry is negative: both fall outside).  One
-        // shared-memory load serves both cases; only a fluid neighbour outside
-        // its window (a periodic wrap) reads global memory.
-        const int32_t row_b = inv(i) * S;               // Q * S < 2^31
-        const WinSpan w = tab[i - 1];
-        const int32_t pos = ee - row_b - w.first;
-        const bool in_win = (unsigned)pos < (unsigned)w.len;
-        const T *src = in_win ? win + (i - 1) * WIN_CELLS + pos : own + i * WIN_TILE + tid;
-        float v = St::raw(*src);
-        if (!in_win && (unsigned)(ee - row_b) < (unsigned)S) v = St::raw(pdf[ee]);
-        g[i] = v;
+        const uint32_t c = code[(i - 1) * WIN_TILE + tid];
+        if (c != WIN_ESCAPE) {
+            const uint32_t pc = c & (WIN_LINK - 1);
+            g[i] = St::raw(pop[pc]);
+            // staged position -> slot: own row i, or column first(2) + offset of row inverse(i)
+            const WinSpan w = tab[i - 1];
+            const int32_t rb = inv(i) * S;
+            const int32_t s1 = rb + w.first - (int32_t)L::OWN_ELEMS - (i - 1) * WIN_CELLS + (int32_t)pc;
+            const int32_t s2 = rb + w.first2 - (int32_t)L::WIN2_ELEMS - (i - 1) * WIN2_CELLS + (int32_t)pc;
+            slot[i] = pc < L::OWN_ELEMS ? i * S + k : (pc < L::WIN2_ELEMS ? s1 : s2);
+            // a boundary link's negative entry (its map), loaded while the cell collides
+            if (HAS_BC && (c & WIN_LINK)) slot[i] = R[(int64_t)(i - 1) * S + k];
+        } else {                                        // a fluid neighbour outside both windows
+            const int32_t e = R[(int64_t)(i - 1) * S + k];
+            slot[i] = e;
+            g[i] = St::raw(pdf[e]);
+        }
     }
     const Vel u = collide<Q, St::scaled>(g, p);
     pdf[k] = St::pack(g[0]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         float v = g[inv(i)];
-        int32_t r = e[i];
+        int32_t r = slot[i];
         if (HAS_BC && r < 0) {
             v = apply_link(maps[-(r + 1)], v, u.x, u.y, u.z, p.scale);
             r = i * S + k;
@@ -200,6 +279,7 @@ template <int Q, int ST, bool HAS_BC, int NSTAGE>
 __global__ void __launch_bounds__(WIN_TILE + 32) aa_odd_window_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                                       const int32_t *__restrict__ R, int32_t S,
                                                                       int32_t nf, const WinSpan *__restrict__ wtab,
+                                                                      const uint16_t *__restrict__ wcode,
                                                                       const LinkMap *__restrict__ maps,
                                                                       CollideParams p, int32_t *err) {
     using T = typename Store<ST>::T;
@@ -227,7 +307,7 @@ __global__ void __launch_bounds__(WIN_TILE + 32) aa_odd_window_kernel(typename S
         uint32_t issued = 0;                         // lane 0: stages whose last copies may be in flight
         uint32_t parity = 0;                         // lane 0: parity of each stage's last issued phase
         auto table_of = [&](int32_t t) -> WinSpan {
-            return (t < n_tiles && lane < Q - 1) ? wtab[(int64_t)t * (Q - 1) + lane] : WinSpan{0, 0};
+            return (t < n_tiles && lane < Q - 1) ? wtab[(int64_t)t * (Q - 1) + lane] : WinSpan{0, 0, 0, 0};
         };
         WinSpan w = table_of(blockIdx.x);
         int j = 0;
@@ -248,7 +328,7 @@ __global__ void __launch_bounds__(WIN_TILE + 32) aa_odd_window_kernel(typename S
             unsigned char *st = wsm + (size_t)s * L::BYTES;
             const bool dir = lane < Q - 1;
             uint32_t bytes = 0;
-            if (dir) bytes += WIN_TILE * 4 + WIN_TILE * sizeof(T) + (uint32_t)w.len * sizeof(T);
+            if (dir) bytes += WIN_TILE * 2 + WIN_TILE * sizeof(T) + (uint32_t)(w.len + w.len2) * sizeof(T);
             if (lane == 0) bytes += WIN_TILE * sizeof(T) + (Q - 1) * sizeof(WinSpan);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
@@ -260,16 +340,19 @@ __global__ void __launch_bounds__(WIN_TILE + 32) aa_odd_window_kernel(typename S
             __syncwarp();
             if (dir) {
                 const int r = lane;
-                bulk_g2s(st + L::IDX + r * WIN_TILE * 4, R + (int64_t)r * S + (int64_t)t * WIN_TILE, WIN_TILE * 4,
+                bulk_g2s(st + L::CODE + r * WIN_TILE * 2, wcode + (int64_t)r * S + (int64_t)t * WIN_TILE, WIN_TILE * 2,
                          &full[s]);
-                bulk_g2s(st + L::OWN + r * WIN_TILE * sizeof(T), pdf + (int64_t)r * S + (int64_t)t * WIN_TILE,
+                bulk_g2s(st + L::POP + r * WIN_TILE * sizeof(T), pdf + (int64_t)r * S + (int64_t)t * WIN_TILE,
                          WIN_TILE * sizeof(T), &full[s]);
                 if (w.len > 0)
-                    bulk_g2s(st + L::WIN + r * WIN_CELLS * sizeof(T), pdf + (int64_t)inv(r + 1) * S + w.first,
-                             (uint32_t)w.len * sizeof(T), &full[s]);
+                    bulk_g2s(st + L::POP + (L::OWN_ELEMS + r * WIN_CELLS) * sizeof(T),
+                             pdf + (int64_t)inv(r + 1) * S + w.first, (uint32_t)w.len * sizeof(T), &full[s]);
+                if (w.len2 > 0)
+                    bulk_g2s(st + L::POP + (L::WIN2_ELEMS + r * WIN2_CELLS) * sizeof(T),
+                             pdf + (int64_t)inv(r + 1) * S + w.first2, (uint32_t)w.len2 * sizeof(T), &full[s]);
             }
             if (lane == 0) {
-                bulk_g2s(st + L::OWN + (Q - 1) * WIN_TILE * sizeof(T),
+                bulk_g2s(st + L::POP + (Q - 1) * WIN_TILE * sizeof(T),
                          pdf + (int64_t)(Q - 1) * S + (int64_t)t * WIN_TILE, WIN_TILE * sizeof(T), &full[s]);
                 bulk_g2s(st + L::TAB, wtab + (int64_t)t * (Q - 1), (Q - 1) * sizeof(WinSpan), &full[s]);
             }
@@ -296,7 +379,7 @@ __global__ void __launch_bounds__(WIN_TILE + 32) aa_odd_window_kernel(typename S
                 break;
             }
             const int32_t k = t * WIN_TILE + tid;
-            if (k < nf) window_cell<Q, ST, HAS_BC>(pdf, wsm + (size_t)s * L::BYTES, tid, k, S, maps, p);
+            if (k < nf) window_cell<Q, ST, HAS_BC>(pdf, R, wsm + (size_t)s * L::BYTES, tid, k, S, maps, p);
             mbar_arrive(&empty[s]);
         }
     }

@@ -175,7 +175,7 @@ static void drop_graphs(Domain &d) {
 
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
-    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.cell_voxel, &d.link_cell,
+    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.win_code, &d.cell_voxel, &d.link_cell,
                       &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask,
                       &d.red_partial, &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
@@ -213,6 +213,7 @@ static slbm_status ensure_window(Domain &d) {
     Ctx cx = d.ctx();
     if (build_window_tab(cx, d) || cx.check(cudaStreamSynchronize(d.stream), "build window table")) {
         cx.release(d.win_tab);
+        cx.release(d.win_code);
         return cx.status == SLBM_OK ? err(SLBM_ECUDA, g_msg) : cx.status;
     }
     return SLBM_OK;

@@ -72,6 +72,7 @@ struct Domain {
     DevBuf code;                       // (Q-1) x S 16-bit link codes of R (sparse)
     DevBuf code_base;                  // (S / CODE_TILE) x (Q-1) column bases of the codes
     DevBuf win_tab;                    // (S / 128) x (Q-1) neighbour windows of the staged odd step
+    DevBuf win_code;                   // (Q-1) x S 16-bit staged positions of R (staged odd step)
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity

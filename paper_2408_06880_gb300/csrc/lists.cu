@@ -515,14 +515,21 @@ int build_link_codes(Ctx &cx, Domain &d) {
 int build_window_tab(Ctx &cx, Domain &d) {
     if (d.S == 0) return 0;
     const int64_t n = d.S / WIN_TILE * (d.q - 1);
-    if (cx.alloc(d.win_tab, n * (int64_t)sizeof(WinSpan))) return -1;
+    if (cx.alloc(d.win_tab, n * (int64_t)sizeof(WinSpan)) ||
+        cx.alloc(d.win_code, (int64_t)(d.q - 1) * d.S * (int64_t)sizeof(uint16_t)))
+        return -1;
     const unsigned grid = (unsigned)((n + 127) / 128);
-    if (d.q == 19)
-        build_window_table<19><<<grid, 128, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid,
-                                                             (WinSpan *)d.win_tab.p);
-    else
-        build_window_table<27><<<grid, 128, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S, (int32_t)d.n_fluid,
-                                                             (WinSpan *)d.win_tab.p);
+    const dim3 cgrid((unsigned)((d.S + 255) / 256), (unsigned)(d.q - 1));
+    const int32_t *R = (const int32_t *)d.P.p;
+    WinSpan *tab = (WinSpan *)d.win_tab.p;
+    uint16_t *code = (uint16_t *)d.win_code.p;
+    if (d.q == 19) {
+        build_window_table<19><<<grid, 128, 0, cx.stream>>>(R, (int32_t)d.S, (int32_t)d.n_fluid, tab);
+        build_window_codes<19><<<cgrid, 256, 0, cx.stream>>>(R, (int32_t)d.S, (int32_t)d.n_fluid, tab, code);
+    } else {
+        build_window_table<27><<<grid, 128, 0, cx.stream>>>(R, (int32_t)d.S, (int32_t)d.n_fluid, tab);
+        build_window_codes<27><<<cgrid, 256, 0, cx.stream>>>(R, (int32_t)d.S, (int32_t)d.n_fluid, tab, code);
+    }
     return cx.check(cudaGetLastError(), "build_window_table launch");
 }
 
