@@ -743,6 +743,15 @@ def _time_pairs(P, d, stream, pairs):
     return e0.elapsed_time(e1) / (2 * pairs)            # ms per LBM step
 
 
+def full_bricks(flags):
+    """Complete 8^3 bricks whose 512 voxels are all fluid (the cells the
+    hybrid cell order steps as dense blocks)."""
+    nz, ny, nx = flags.shape
+    f = flags[:nz // 8 * 8, :ny // 8 * 8, :nx // 8 * 8] == 0
+    f = f.reshape(nz // 8, 8, ny // 8, 8, nx // 8, 8)
+    return int(np.count_nonzero(f.all(axis=(1, 3, 5))))
+
+
 def run_workloads(a, pairs=10):
     """The application-shaped workloads (stand-ins for Sec. 6.2 and 6.3):
     the 512 x 256 x 256 particle bed (D3Q27 TRT, velocity inlet, pressure
@@ -758,16 +767,26 @@ def run_workloads(a, pairs=10):
     peak, _ = load_peaks()
     out = {"mode": "workloads", "data": "synthetic", "peak_gbs": peak, "rows": []}
 
-    def row(name, g, q, storage, layout=P.SPARSE, flags=None):
+    def row(name, g, q, storage, layout=P.SPARSE, flags=None, order=P.ORDER_LEX):
         b = 4 if storage == P.FP32 else 2
         d = P.Domain(g.flags if flags is None else flags, periodic=g.periodic,
                      inlet_u=g.inlet_u if flags is None else None, rho_out=g.rho_out, q=q, op=P.TRT, omega=OMEGA,
                      trt_magic=MAGIC, storage=storage, scale_exp=P.auto_scale_exp(0.06) if storage else 0,
-                     layout=layout, stream=stream)
+                     layout=layout, stream=stream, cell_order=order)
         ms = _time_pairs(P, d, stream, pairs)
         nf = int(np.count_nonzero(g.flags == 0))
         per = (2 * q * b + (q - 1) * B_IDX / 2) if layout == P.SPARSE else None
+        extra = {}
+        if order == P.ORDER_HYBRID:
+            # index bytes of the odd step: every link of the sparse cells, the
+            # face links of the full bricks
+            n_full = full_bricks(g.flags)
+            faces = {19: 1824, 27: 3176}[q]
+            idx = ((nf - 512 * n_full) * (q - 1) + n_full * faces) * B_IDX
+            per = 2 * q * b + idx / nf / 2
+            extra = {"full_brick_cells": 512 * n_full, "full_brick_share": round(512 * n_full / nf, 4)}
         r = {"workload": name, "q": q, "storage": {P.FP32: "fp32", P.FP16: "fp16"}[storage],
+             "cell_order": {P.ORDER_LEX: "lex", P.ORDER_BRICK8: "brick8", P.ORDER_HYBRID: "hybrid"}[order], **extra,
              "layout": {P.SPARSE: "sparse", P.DENSE: "dense"}[layout], "n_voxels": int(g.flags.size),
              "n_fluid": nf, "fluid_fraction": round(nf / g.flags.size, 5),
              "mflups": round(nf / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
@@ -782,6 +801,8 @@ def run_workloads(a, pairs=10):
     bed = G.particle_bed()
     row("particle bed 512x256x256", bed, 27, P.FP32)
     row("particle bed 512x256x256", bed, 27, P.FP16)
+    row("particle bed 512x256x256 (hybrid: full bricks dense)", bed, 27, P.FP32, order=P.ORDER_HYBRID)
+    row("particle bed 512x256x256 (hybrid: full bricks dense)", bed, 27, P.FP16, order=P.ORDER_HYBRID)
     art = G.artery_tree()
     row("artery tree 1024x512x512", art, 19, P.FP32)
     walls = np.where(art.flags >= G.INLET, np.uint8(G.WALL), art.flags).astype(np.uint8)

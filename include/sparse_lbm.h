@@ -68,7 +68,7 @@ enum { SLBM_SRT = 0, SLBM_TRT = 1, SLBM_MRT = 2 };
 enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
 enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1, SLBM_LAYOUT_SPARSE_PULL = 2 };
 enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
-enum { SLBM_ORDER_LEX = 0, SLBM_ORDER_BRICK8 = 1 };
+enum { SLBM_ORDER_LEX = 0, SLBM_ORDER_BRICK8 = 1, SLBM_ORDER_HYBRID = 2 };
 enum { SLBM_ORDER_CELLS = 0, SLBM_ORDER_VOXELS = 1 };
 
 /* Problem description (Sec. 2 parameters, Sec. 3 geometry). */

@@ -138,7 +138,7 @@ class Problem:
     inlet_u: np.ndarray | None = None
     rho_out: float = 1.0
     mrt_rates: tuple | None = None    # MRT: 19 per-moment rates (default mrt_default_rates)
-    order: int = 0                    # cell order: 0 lexicographic, 1 brick-8
+    order: int = 0                    # cell order: 0 lexicographic, 1 brick-8, 2 full bricks first
 
     @classmethod
     def from_geometry(cls, g, **kw):
@@ -250,8 +250,9 @@ def stride_of(nf: int) -> int:
 
 
 def compact(p: Problem):
-    """Compacted fluid-cell order (Sec. 3.1), lexicographic or brick-8 by
-    `p.order`: (cell_id[N], cell_voxel[N_F])."""
+    """Compacted fluid-cell order (Sec. 3.1) by `p.order`: lexicographic,
+    brick-8, or full 8^3 bricks first then the rest in brick-8 order:
+    (cell_id[N], cell_voxel[N_F])."""
     cid = np.zeros(p.n, np.int32)
     cvx = np.zeros(max(p.n, 1), np.int32)
     nf = lib().orc_compact(p._c(), _ptr(cid), _ptr(cvx))

@@ -394,19 +394,38 @@ static void visit(const orc_problem *p, int64_t v, int64_t *k, int32_t *cell_id,
     }
 }
 
+/* A brick is "full" when it lies wholly inside the box (8x8x8 voxels) and
+ * every voxel of it is fluid. */
+static int brick_full(const orc_problem *p, int bx, int by, int bz) {
+    if (bx + 8 > p->nx || by + 8 > p->ny || bz + 8 > p->nz) return 0;
+    for (int z = bz; z < bz + 8; ++z)
+        for (int y = by; y < by + 8; ++y)
+            for (int x = bx; x < bx + 8; ++x)
+                if (p->flags[x + (int64_t)p->nx * (y + (int64_t)p->ny * z)] != ORC_FLUID) return 0;
+    return 1;
+}
+
+/* order 2 ("hybrid"): first the full bricks, in lexicographic brick order
+ * and lexicographic inside each; then every other fluid voxel in the brick-8
+ * order (the full bricks skipped).  The cells of a full brick are 512
+ * consecutive cells, whose neighbours inside the brick follow from the cell
+ * number alone (the dense part of a hybrid sparse/dense layout, Sec. 4.1). */
 int64_t orc_compact(const orc_problem *p, int32_t *cell_id, int32_t *cell_voxel) {
     int64_t n = nvox(p), k = 0;
     if (p->order == 0) {
         for (int64_t v = 0; v < n; ++v) visit(p, v, &k, cell_id, cell_voxel);
         return k;
     }
-    for (int bz = 0; bz < p->nz; bz += 8)
-        for (int by = 0; by < p->ny; by += 8)
-            for (int bx = 0; bx < p->nx; bx += 8)
-                for (int z = bz; z < bz + 8 && z < p->nz; ++z)
-                    for (int y = by; y < by + 8 && y < p->ny; ++y)
-                        for (int x = bx; x < bx + 8 && x < p->nx; ++x)
-                            visit(p, x + (int64_t)p->nx * (y + (int64_t)p->ny * z), &k, cell_id, cell_voxel);
+    for (int pass = (p->order == 2 ? 0 : 1); pass < 2; ++pass)
+        for (int bz = 0; bz < p->nz; bz += 8)
+            for (int by = 0; by < p->ny; by += 8)
+                for (int bx = 0; bx < p->nx; bx += 8) {
+                    if (p->order == 2 && brick_full(p, bx, by, bz) != (pass == 0)) continue;
+                    for (int z = bz; z < bz + 8 && z < p->nz; ++z)
+                        for (int y = by; y < by + 8 && y < p->ny; ++y)
+                            for (int x = bx; x < bx + 8 && x < p->nx; ++x)
+                                visit(p, x + (int64_t)p->nx * (y + (int64_t)p->ny * z), &k, cell_id, cell_voxel);
+                }
     return k;
 }
 

@@ -14,7 +14,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EDIVERGED, ETIMEOUT, EABORTED, EDEVICE 
 SRT, TRT, MRT = 0, 1, 2
 FP32, FP16, BF16 = 0, 1, 2
 SPARSE, DENSE, SPARSE_PULL = 0, 1, 2
-ORDER_LEX, ORDER_BRICK8 = 0, 1
+ORDER_LEX, ORDER_BRICK8, ORDER_HYBRID = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 ORDER_CELLS, ORDER_VOXELS = 0, 1
 NOALLOC_MAX_VOXELS = 268435456

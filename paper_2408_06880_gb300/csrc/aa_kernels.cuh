@@ -205,12 +205,12 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
                                             int32_t S, int32_t nf, const LinkMap *__restrict__ maps,
                                             int32_t n_links, const CollideParams &p, int32_t *err,
                                             int32_t pf_dist, const uint16_t *__restrict__ code,
-                                            const int32_t *__restrict__ cbase) {
+                                            const int32_t *__restrict__ cbase, int32_t k_first = 0) {
     using St = Store<ST>;
     using T = typename St::T;
     const int32_t span = blockDim.x * CPT;
     if (pf_dist > 0 && threadIdx.x == 0) {
-        const int64_t c0 = ((int64_t)blockIdx.x + pf_dist) * span;
+        const int64_t c0 = k_first + ((int64_t)blockIdx.x + pf_dist) * span;
         if (c0 < nf) {
             const int64_t left = (int64_t)S - c0;
             const uint32_t cells = (uint32_t)(left < (int64_t)span ? left : (int64_t)span);
@@ -221,7 +221,7 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
             }
         }
     }
-    const int32_t kb = blockIdx.x * span + threadIdx.x;
+    const int32_t kb = k_first + blockIdx.x * span + threadIdx.x;
     // CODE: every lane stays to the end of the decode (warp shuffles)
     if (!CODE && kb >= nf) return;
     int32_t e[CPT][Q];
@@ -328,6 +328,18 @@ __global__ void __launch_bounds__(256) aa_odd_kernel(typename Store<ST>::T *__re
                                                      const int32_t *__restrict__ cbase = nullptr) {
     aa_odd_body<Q, ST, CPT, HAS_BC, CHECK, RELOAD, CODE, OP>(pdf, P, S, nf, maps, n_links, p, err, pf_dist, code,
                                                               cbase);
+}
+
+// The plain odd kernel (1 cell per thread, L2 index prefetch) over the cells
+// k_first .. nf-1 only (the sparse part of the hybrid cell order).
+template <int Q, int ST, bool HAS_BC>
+__global__ void __launch_bounds__(256) aa_odd_kernel_from(typename Store<ST>::T *__restrict__ pdf,
+                                                          const int32_t *__restrict__ P, int32_t S, int32_t nf,
+                                                          const LinkMap *__restrict__ maps, int32_t n_links,
+                                                          CollideParams p, int32_t *err, int32_t pf_dist,
+                                                          int32_t k_first) {
+    aa_odd_body<Q, ST, 1, HAS_BC, false, false, false, OP_TRT>(pdf, P, S, nf, maps, n_links, p, err, pf_dist, nullptr,
+                                                                nullptr, k_first);
 }
 
 // The plain odd kernel (1 cell per thread, L2 index prefetch) held to 64

@@ -6,6 +6,7 @@
 
 #include "aa_kernels.cuh"
 #include "aa_window.cuh"
+#include "brick.cuh"
 #include "internal.h"
 
 namespace slbm {
@@ -258,6 +259,21 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
                       : (bc ? aa_odd_kernel<Q, ST, 2, true, false, false, true> : aa_odd_kernel<Q, ST, 2, false, false, false, true>);
         const int32_t pfc = (int32_t)persistent_grid(kc, sh.threads, INT32_MAX);
         kc<<<grid(sh.cells), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfc, code, cb);
+        return cudaGetLastError();
+    }
+    // hybrid cell order: the full bricks by arithmetic and their face lists,
+    // the other cells (numbered after them) with the plain odd kernel
+    if (d.order == SLBM_ORDER_HYBRID && d.n_full_cells > 0) {
+        const int32_t nfull = (int32_t)d.n_full_cells;
+        auto kf = bc ? aa_odd_brick_kernel<Q, ST, true> : aa_odd_brick_kernel<Q, ST, false>;
+        const int32_t pff = (int32_t)persistent_grid(kf, 128, INT32_MAX);
+        kf<<<(unsigned)((nfull + 127) / 128), 128, 0, st>>>(pdf, reinterpret_cast<const int32_t *>(d.face.p), S, nfull,
+                                                             maps, p, pff);
+        if (nf > nfull) {
+            auto kr = bc ? aa_odd_kernel_from<Q, ST, true> : aa_odd_kernel_from<Q, ST, false>;
+            const int32_t pfr = (int32_t)persistent_grid(kr, 128, INT32_MAX);
+            kr<<<(unsigned)((nf - nfull + 127) / 128), 128, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfr, nfull);
+        }
         return cudaGetLastError();
     }
     // variant 6: every read of a tile staged in shared memory (index rows, own

@@ -175,7 +175,7 @@ static void drop_graphs(Domain &d) {
 
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
-    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.win_code, &d.cell_voxel, &d.link_cell,
+    DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.win_code, &d.face, &d.cell_voxel, &d.link_cell,
                       &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask,
                       &d.red_partial, &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
@@ -252,7 +252,8 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (s.scale_exp < -40 || s.scale_exp > 40) return err(SLBM_EINVAL, "scale_exp must lie in [-40, 40]");
     if (s.layout != SLBM_LAYOUT_SPARSE && s.layout != SLBM_LAYOUT_DENSE && s.layout != SLBM_LAYOUT_SPARSE_PULL)
         return err(SLBM_EINVAL, "bad layout");
-    if (s.order != SLBM_ORDER_LEX && s.order != SLBM_ORDER_BRICK8) return err(SLBM_EINVAL, "order must be 0 or 1");
+    if (s.order != SLBM_ORDER_LEX && s.order != SLBM_ORDER_BRICK8 && s.order != SLBM_ORDER_HYBRID)
+        return err(SLBM_EINVAL, "order must be 0, 1 or 2");
     if (s.order != SLBM_ORDER_LEX && s.layout == SLBM_LAYOUT_DENSE)
         return err(SLBM_EUNSUPPORTED, "the dense layout has no cell order");
     for (int a = 0; a < 3; ++a)
@@ -634,6 +635,9 @@ slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, in
         return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
     if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
         return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
+    if (parity == 1 && h->d.order == SLBM_ORDER_HYBRID && h->d.layout == SLBM_LAYOUT_SPARSE &&
+        !(threads == 128 && cells == 1 && variant == 2))
+        return err(SLBM_EUNSUPPORTED, "the hybrid cell order has one odd-step shape (full bricks + 128 x 1, variant 2)");
     if (variant == 0) {
         if (threads < 32 || threads > 256 || threads % 32)
             return err(SLBM_EINVAL, "threads must be 32..256, multiple of 32");

@@ -73,6 +73,8 @@ struct Domain {
     DevBuf code_base;                  // (S / CODE_TILE) x (Q-1) column bases of the codes
     DevBuf win_tab;                    // (S / 128) x (Q-1) neighbour windows of the staged odd step
     DevBuf win_code;                   // (Q-1) x S 16-bit staged positions of R (staged odd step)
+    DevBuf face;                       // face links of the full bricks (hybrid order)
+    int64_t n_full_cells = 0;          // hybrid order: cells of the full bricks (512 each), numbered first
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity

@@ -6,6 +6,7 @@
 // so cell k is the k-th fluid voxel in ascending id: exactly the order of a
 // sequential scan, whatever the launch shape (integer sums are exact).
 #include "aa_window.cuh"
+#include "brick.cuh"
 #include "internal.h"
 
 namespace slbm {
@@ -157,6 +158,62 @@ struct BrickCompaction {
         if (val) cell_voxel[ex] = (int32_t)v;
     }
 };
+
+// Hybrid cell order (SLBM_ORDER_HYBRID): the full bricks first (brick j of
+// them holds cells 512 j .. 512 j + 511, voxels lexicographic inside), then
+// every other fluid voxel in brick-8 order.  A brick is full when it lies
+// wholly inside the box and its 512 voxels are fluid.
+__global__ void brick_full_kernel(const uint8_t *flags, int32_t nx, int32_t ny, int32_t nz, int32_t nbx, int32_t nby,
+                                  int64_t n_bricks, uint8_t *full) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bricks) return;
+    const int x0 = (int)(b % nbx) * 8, y0 = (int)((b / nbx) % nby) * 8, z0 = (int)(b / ((int64_t)nbx * nby)) * 8;
+    uint8_t f = x0 + 8 <= nx && y0 + 8 <= ny && z0 + 8 <= nz;
+    for (int l = 0; l < 512 && f; ++l) {
+        const int64_t v = (x0 + (l & 7)) + (int64_t)nx * ((y0 + ((l >> 3) & 7)) + (int64_t)ny * (z0 + (l >> 6)));
+        f = flags[v] == FLAG_FLUID;
+    }
+    full[b] = f;
+}
+
+struct FullBrickScan {             // rank of each full brick among the full ones
+    const uint8_t *full;
+    int32_t *rank;
+    __device__ int32_t value(int64_t b) const { return full[b]; }
+    __device__ void emit(int64_t b, int32_t val, int32_t ex) const { rank[b] = val ? ex : -1; }
+};
+
+// The fluid voxels of the other bricks, numbered from `base` in brick-8 order.
+struct HybridRestCompaction {
+    BrickCompaction brick;
+    const uint8_t *full;
+    int32_t base;
+    __device__ int32_t value(int64_t pos) const { return !full[pos >> 9] && brick.value(pos); }
+    __device__ void emit(int64_t pos, int32_t val, int32_t ex) const {
+        if (full[pos >> 9]) return;
+        const int64_t v = brick.voxel(pos);
+        if (v < 0) return;
+        brick.cell_id[v] = val ? base + ex : -1;
+        if (val) brick.cell_voxel[base + ex] = (int32_t)v;
+    }
+};
+
+// Cells of the full bricks: thread per (brick, local voxel).
+__global__ void emit_full_bricks(const int32_t *rank, int32_t nx, int32_t ny, int32_t nbx, int32_t nby,
+                                 int64_t n_bricks, int32_t *cell_id, int32_t *cell_voxel) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_bricks * 512) return;
+    const int64_t b = t >> 9;
+    const int32_t r = rank[b];
+    if (r < 0) return;
+    const int l = (int)(t & 511);
+    const int x = (int)(b % nbx) * 8 + (l & 7), y = (int)((b / nbx) % nby) * 8 + ((l >> 3) & 7),
+              z = (int)(b / ((int64_t)nbx * nby)) * 8 + (l >> 6);
+    const int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+    const int32_t k = r * 512 + l;
+    cell_id[v] = k;
+    cell_voxel[k] = (int32_t)v;
+}
 
 struct InletList {                 // ascending voxel ids of inlet voxels
     const uint8_t *flags;
@@ -348,6 +405,31 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
                                          nbx, nby},
                      positions, &nf))
             return -1;
+    } else if (d.order == SLBM_ORDER_HYBRID) {
+        const int32_t nbx = (d.nx + 7) / 8, nby = (d.ny + 7) / 8, nbz = (d.nz + 7) / 8;
+        const int64_t n_bricks = (int64_t)nbx * nby * nbz;
+        DevBuf full, rank;
+        if (cx.alloc(full, n_bricks) || cx.alloc(rank, n_bricks * sizeof(int32_t))) return -1;
+        brick_full_kernel<<<(unsigned)((n_bricks + 127) / 128), 128, 0, cx.stream>>>(
+            d_flags, d.nx, d.ny, d.nz, nbx, nby, n_bricks, (uint8_t *)full.p);
+        int64_t n_full = 0, rest = 0;
+        if (cx.check(cudaGetLastError(), "brick_full launch") ||
+            scan_run(cx, FullBrickScan{(const uint8_t *)full.p, (int32_t *)rank.p}, n_bricks, &n_full))
+            return -1;
+        if (n_full > 0) {
+            emit_full_bricks<<<(unsigned)((n_bricks * 512 + 255) / 256), 256, 0, cx.stream>>>(
+                (const int32_t *)rank.p, d.nx, d.ny, nbx, nby, n_bricks, (int32_t *)cell_id.p,
+                (int32_t *)d.cell_voxel.p);
+            if (cx.check(cudaGetLastError(), "emit_full_bricks launch")) return -1;
+        }
+        const BrickCompaction bc{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p, d.nx, d.ny, d.nz, nbx, nby};
+        if (scan_run(cx, HybridRestCompaction{bc, (const uint8_t *)full.p, (int32_t)(n_full * 512)}, n_bricks * 512,
+                     &rest))
+            return -1;
+        cx.release(full);
+        cx.release(rank);
+        d.n_full_cells = n_full * 512;
+        nf = d.n_full_cells + rest;
     } else if (scan_run(cx, FluidCompaction{d_flags, (int32_t *)cell_id.p, (int32_t *)d.cell_voxel.p}, N, &nf)) {
         return -1;
     }
@@ -420,6 +502,18 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
     else launch(std::integral_constant<int, 27>{});
     if (cx.check(cudaGetLastError(), "build_index launch") || cx.check(cudaStreamSynchronize(cx.stream), "build sync"))
         return -1;
+    if (d.order == SLBM_ORDER_HYBRID && d.layout == SLBM_LAYOUT_SPARSE && d.n_full_cells > 0) {   // face lists
+        const int64_t entries = d.n_full_cells / 512 * (d.q == 19 ? face_block<19>() : face_block<27>());
+        if (cx.alloc(d.face, entries * sizeof(int32_t))) return -1;
+        const unsigned gf = (unsigned)((d.n_full_cells + 255) / 256);
+        if (d.q == 19)
+            build_face_list<19><<<gf, 256, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S,
+                                                           (int32_t)d.n_full_cells, (int32_t *)d.face.p);
+        else
+            build_face_list<27><<<gf, 256, 0, cx.stream>>>((const int32_t *)d.P.p, (int32_t)d.S,
+                                                           (int32_t)d.n_full_cells, (int32_t *)d.face.p);
+        if (cx.check(cudaGetLastError(), "build_face_list launch")) return -1;
+    }
     if (n_links > 0) {   // cells with links, for the fix-up around the even step
         if (cx.alloc(d.bcell, n_links * 4) || cx.alloc(d.bfirst, (n_links + 1) * 4)) return -1;
         int64_t nb = 0;

@@ -17,27 +17,31 @@ DIRS27 = DIRS19 + [(1, 1, 1), (-1, -1, -1), (1, 1, -1), (-1, -1, 1), (1, -1, 1),
                    (-1, 1, 1), (1, -1, -1)]
 
 
-def visiting_order(nx, ny, nz, brick):
-    """Voxels (x, y, z) in cell-numbering order: lexicographic, or brick-8
-    (8^3 bricks lexicographic, voxels lexicographic inside each brick)."""
+def visiting_order(nx, ny, nz, brick, flags=None):
+    """Voxels (x, y, z) in cell-numbering order: lexicographic (0), brick-8
+    (1: 8^3 bricks lexicographic, voxels lexicographic inside each brick), or
+    full bricks first (2: the bricks of 512 fluid voxels in brick-8 order,
+    then every other voxel in brick-8 order)."""
     if not brick:
         return [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx)]
-    out = []
+    bricks = []
     for bz in range(0, nz, 8):
         for by in range(0, ny, 8):
             for bx in range(0, nx, 8):
-                for z in range(bz, min(bz + 8, nz)):
-                    for y in range(by, min(by + 8, ny)):
-                        for x in range(bx, min(bx + 8, nx)):
-                            out.append((x, y, z))
-    return out
+                vox = [(x, y, z) for z in range(bz, min(bz + 8, nz)) for y in range(by, min(by + 8, ny))
+                       for x in range(bx, min(bx + 8, nx))]
+                bricks.append(vox)
+    if brick == 1:
+        return [v for b in bricks for v in b]
+    full = [len(b) == 512 and all(flags[z, y, x] == G.FLUID for x, y, z in b) for b in bricks]
+    return [v for b, f in zip(bricks, full) if f for v in b] + [v for b, f in zip(bricks, full) if not f for v in b]
 
 
 def brute_force_lists(g, q, brick=0):
     dirs = DIRS19 if q == 19 else DIRS27
     nz, ny, nx = g.flags.shape
     fl = g.flags
-    order = [(x, y, z) for x, y, z in visiting_order(nx, ny, nz, brick) if fl[z, y, x] == G.FLUID]
+    order = [(x, y, z) for x, y, z in visiting_order(nx, ny, nz, brick, fl) if fl[z, y, x] == G.FLUID]
     index = {v: k for k, v in enumerate(order)}
     nf = len(order)
     S = (nf + 127) // 128 * 128
@@ -89,8 +93,30 @@ BRICK_CASES = [
 ]
 
 
+def _half_solid(seed):
+    # 24 x 17 x 20 box: solids only in the lower z layers and in one corner,
+    # so some complete bricks are all fluid (full) and others not; partial
+    # bricks at the high faces; inlet/outlet planes at x = 0 and x = 23
+    g = G.random_solids((24, 17, 20), 0.0, seed, periodic=0b010)
+    f = g.flags
+    rng = np.random.default_rng(seed)
+    f[:6] = np.where(rng.random(f[:6].shape) < 0.4, G.WALL, G.FLUID)
+    f[14:, 10:, 16:] = G.WALL
+    f[:, :, 0] = np.where(f[:, :, 0] == G.FLUID, G.INLET, f[:, :, 0])
+    f[:, :, -1] = np.where(f[:, :, -1] == G.FLUID, G.OUTLET, f[:, :, -1])
+    g.inlet_u = rng.uniform(-0.05, 0.05, (int(np.count_nonzero(f == G.INLET)), 3))
+    return g
+
+
+HYBRID_CASES = [
+    ("hybrid_periodic", lambda s: G.random_solids((16, 24, 17), 0.0 if s == 0 else 0.004, s, periodic=7)),
+    ("hybrid_half_solid", _half_solid),
+]
+
+
 @pytest.mark.parametrize("q", [19, 27])
-@pytest.mark.parametrize("name,make,brick", [c + (0,) for c in CASES] + [c + (1,) for c in BRICK_CASES])
+@pytest.mark.parametrize("name,make,brick", [c + (0,) for c in CASES] + [c + (1,) for c in BRICK_CASES] +
+                         [c + (2,) for c in HYBRID_CASES])
 def test_lists_match_brute_force(q, name, make, brick):
     c, _, _ = O.stencil(q)
     assert [tuple(v) for v in c] == (DIRS19 if q == 19 else DIRS27)
@@ -155,10 +181,11 @@ SPARSE_DENSE = [
     ("walled_trt", lambda: G.random_solids(8, 0.25, 12, periodic=0b011, walls_z=True), O.TRT),
     ("mixed_bc_trt", lambda: _mixed_geometry(13), O.TRT),
     ("partial_bricks_trt", lambda: G.random_solids((19, 10, 17), 0.3, 14, periodic=0b101), O.TRT),
+    ("full_bricks_trt", lambda: _half_solid(15), O.TRT),
 ]
 
 
-@pytest.mark.parametrize("brick", [0, 1])
+@pytest.mark.parametrize("brick", [0, 1, 2])
 @pytest.mark.parametrize("q", [19, 27])
 @pytest.mark.parametrize("name,make,op", SPARSE_DENSE)
 def test_sparse_equals_dense_bitwise(q, name, make, op, brick):
