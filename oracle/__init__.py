@@ -10,8 +10,9 @@ Contents (each function cites the passage it follows):
 
 * ``oracle.c`` (plain C, FP64, compiled here with gcc): stencils, Eq. 1
   moments, Eq. 6 equilibrium, Eq. 5 SRT / textbook TRT / D3Q19 MRT (the
-  orthogonal moment basis of d'Humieres et al. 2002; Sec. 4 lists MRT among
-  the operators) collision with a Guo force, a dense direct-addressing
+  orthogonal moment basis of d'Humieres et al. 2002) / D3Q27 central-moment
+  and cumulant (Geier et al. 2015) collisions with a Guo force (Sec. 4 lists
+  these operators, Sec. 5.1 benchmarks them), a dense direct-addressing
   two-grid PUSH stepper (Sec. 2-3), the
   compacted cell order and the pull index-list (Sec. 3.1, 3.1.1) and a sparse
   two-grid PULL stepper on that list.
@@ -41,7 +42,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-SRT, TRT, MRT = 0, 1, 2
+SRT, TRT, MRT, CM, CUMULANT = 0, 1, 2, 3, 4
 FLUID, WALL, INLET, OUTLET = 0, 1, 2, 3
 PAD = np.iinfo(np.int32).min
 
@@ -63,7 +64,8 @@ class _Problem(C.Structure):
                 ("flags", C.c_void_p), ("periodic", C.c_uint32), ("q", C.c_int32),
                 ("op", C.c_int32), ("omega_plus", C.c_double), ("omega_minus", C.c_double),
                 ("force", C.c_double * 3), ("inlet_u", C.c_void_p), ("rho_out", C.c_double),
-                ("mrt_s", C.c_double * 19), ("order", C.c_int32)]
+                ("mrt_s", C.c_double * 19), ("order", C.c_int32), ("cm_bulk", C.c_double),
+                ("cm_high", C.c_double)]
 
 
 def lib():
@@ -79,6 +81,9 @@ def lib():
             L.orc_moments.argtypes = [C.c_int, vp, vp, vp, vp]
             L.orc_collide.argtypes = [P, vp, vp]
             L.orc_mrt_matrix.argtypes = [vp]
+            L.orc_central_moments.argtypes = [vp, vp, vp]
+            L.orc_from_central.argtypes = [vp, vp, vp]
+            L.orc_cumulants.argtypes = [P, vp, vp]
             L.orc_dense_init.argtypes = [P, vp, vp, vp]
             L.orc_dense_run.argtypes = [P, vp, C.c_int]
             L.orc_dense_macroscopic.argtypes = [P, vp, vp, vp]
@@ -138,6 +143,8 @@ class Problem:
     inlet_u: np.ndarray | None = None
     rho_out: float = 1.0
     mrt_rates: tuple | None = None    # MRT: 19 per-moment rates (default mrt_default_rates)
+    cm_bulk: float = 1.0              # CM / CUMULANT (D3Q27): rate of the trace of the second moments
+    cm_high: float = 1.0              # CM / CUMULANT: rate of the moments (cumulants) of orders 3..6
     order: int = 0                    # cell order: 0 lexicographic, 1 brick-8, 2 full bricks first
 
     @classmethod
@@ -171,10 +178,13 @@ class Problem:
         nx, ny, nz = self.shape
         if self.op == MRT and self.q != 19:
             raise ValueError("the MRT operator is defined for D3Q19")
+        if self.op in (CM, CUMULANT) and self.q != 27:
+            raise ValueError("the central-moment and cumulant operators are defined for D3Q27")
         rates = self.mrt_rates if self.mrt_rates is not None else mrt_default_rates(self.omega_plus)
         s = _Problem(nx, ny, nz, _ptr(self._flags_c), self.periodic, self.q, self.op,
                      self.omega_plus, self.omega_minus, (C.c_double * 3)(*self.force),
-                     _ptr(self._inlet_c), self.rho_out, (C.c_double * 19)(*rates), self.order)
+                     _ptr(self._inlet_c), self.rho_out, (C.c_double * 19)(*rates), self.order,
+                     self.cm_bulk, self.cm_high)
         self._cs = s
         return C.byref(s)
 
@@ -204,6 +214,33 @@ def guo_source(q: int, u, F) -> np.ndarray:
     F = np.ascontiguousarray(F, np.float64)
     out = np.zeros(q)
     lib().orc_guo_source(q, _ptr(u), _ptr(F), _ptr(out))
+    return out
+
+
+def central_moments(f, u) -> np.ndarray:
+    """D3Q27 central moments about u: [a + 3b + 9c] = sum f (cx-ux)^a (cy-uy)^b (cz-uz)^c."""
+    f = np.ascontiguousarray(f, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    out = np.zeros(27)
+    lib().orc_central_moments(_ptr(f), _ptr(u), _ptr(out))
+    return out
+
+
+def from_central(kap, u) -> np.ndarray:
+    """The D3Q27 populations with the given central moments about u."""
+    kap = np.ascontiguousarray(kap, np.float64)
+    u = np.ascontiguousarray(u, np.float64)
+    out = np.zeros(27)
+    lib().orc_from_central(_ptr(kap), _ptr(u), _ptr(out))
+    return out
+
+
+def cumulants(p: Problem, f) -> np.ndarray:
+    """Normalised cumulants (orders >= 2, moment indexing) of one D3Q27 cell
+    about its Guo velocity; orders 0 and 1 as 0."""
+    f = np.ascontiguousarray(f, np.float64)
+    out = np.zeros(27)
+    lib().orc_cumulants(p._c(), _ptr(f), _ptr(out))
     return out
 
 

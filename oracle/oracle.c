@@ -40,7 +40,7 @@
 #endif
 
 enum { ORC_FLUID = 0, ORC_WALL = 1, ORC_INLET = 2, ORC_OUTLET = 3 };
-enum { ORC_SRT = 0, ORC_TRT = 1, ORC_MRT = 2 };
+enum { ORC_SRT = 0, ORC_TRT = 1, ORC_MRT = 2, ORC_CM = 3, ORC_CUM = 4 };
 
 /* Velocity set, directions written out one by one (D3Q19 is the first 19
  * rows of D3Q27).  Ordering convention: rest, then the six axis directions,
@@ -66,7 +66,9 @@ typedef struct {
     const double *inlet_u;     /* 3 per inlet voxel, ascending voxel order; may be NULL */
     double rho_out;            /* outlet density */
     double mrt_s[19];          /* ORC_MRT (D3Q19): relaxation rate of each moment of the basis below */
-    int32_t order;             /* cell order: 0 lexicographic, 1 brick-8 (see orc_compact) */
+    int32_t order;             /* cell order: 0 lexicographic, 1 brick-8, 2 full bricks first (orc_compact) */
+    double cm_bulk;            /* ORC_CM / ORC_CUM (D3Q27): rate of the trace of the second-order moments */
+    double cm_high;            /* ORC_CM / ORC_CUM: rate of every moment (cumulant) of order 3..6 */
 } orc_problem;
 
 /* ---------------------------------------------------------------- stencil */
@@ -204,6 +206,208 @@ static void collide_mrt(const orc_problem *p, const double *f, const double *feq
     }
 }
 
+/* ------------------------------------------- central-moment and cumulant
+ * collisions (D3Q27; Sec. 4 lists both among the generated operators, Sec.
+ * 5.1 benchmarks them; definitions: central moments about the Guo velocity
+ * u, cumulants of Geier et al. 2015, both with the density factored out of
+ * orders >= 2).
+ *
+ * Central moments: kap[a + 3b + 9c] = sum_i f_i (cx_i - ux)^a (cy_i - uy)^b
+ * (cz_i - uz)^c, a, b, c in {0, 1, 2}.  With u = (j + F/2)/rho the first
+ * ones are -F/2.  The collision keeps kap_000 = rho, sets the first ones to
+ * +F/2 (the momentum gains F), relaxes the second ones -- the trace with
+ * cm_bulk towards 3 rho c_s^2, the two normal differences and the three
+ * off-diagonal ones with omega_plus towards 0 -- and the moments of order
+ * 3..6 with cm_high: towards rho * prod m(.) with m(0) = 1, m(1) = 0,
+ * m(2) = 1/3 (the factorised equilibrium of D3Q27) for ORC_CM; for ORC_CUM
+ * their cumulants (of the normalised central moments kap/rho, the first
+ * ones taken as zero) towards 0.  Back to f through the inverse of the
+ * central-moment map. */
+static double ipow3(double x, int n) { return n == 0 ? 1.0 : (n == 1 ? x : x * x); }
+
+void orc_central_moments(const double *f, const double u[3], double *kap) {
+    for (int m = 0; m < 27; ++m) {
+        int a = m % 3, b = (m / 3) % 3, c = m / 9;
+        double s = 0.0;
+        for (int i = 0; i < 27; ++i)
+            s += f[i] * ipow3(VEL[i][0] - u[0], a) * ipow3(VEL[i][1] - u[1], b) * ipow3(VEL[i][2] - u[2], c);
+        kap[m] = s;
+    }
+}
+
+/* Inverse of the 3 x 3 map k_alpha = sum_c (c - u)^alpha f_c, c = -1, 0, 1,
+ * by Gauss-Jordan elimination with partial pivoting: Ai[c + 1][alpha]. */
+static void inverse_1d(double u, double Ai[3][3]) {
+    double A[3][6];
+    for (int al = 0; al < 3; ++al)
+        for (int c = 0; c < 3; ++c) {
+            A[al][c] = ipow3((double)(c - 1) - u, al);
+            A[al][3 + c] = al == c ? 1.0 : 0.0;
+        }
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        for (int k = 0; k < 6; ++k) {
+            double t = A[col][k];
+            A[col][k] = A[piv][k];
+            A[piv][k] = t;
+        }
+        double d = A[col][col];
+        for (int k = 0; k < 6; ++k) A[col][k] /= d;
+        for (int r = 0; r < 3; ++r) {
+            if (r == col) continue;
+            double e = A[r][col];
+            for (int k = 0; k < 6; ++k) A[r][k] -= e * A[col][k];
+        }
+    }
+    /* A^-1 maps (k_0, k_1, k_2) to (f_-1, f_0, f_1): its rows are indexed by c */
+    for (int c = 0; c < 3; ++c)
+        for (int al = 0; al < 3; ++al) Ai[c][al] = A[c][3 + al];
+}
+
+void orc_from_central(const double *kap, const double u[3], double *f) {
+    double X[3][3], Y[3][3], Z[3][3];
+    inverse_1d(u[0], X);
+    inverse_1d(u[1], Y);
+    inverse_1d(u[2], Z);
+    for (int i = 0; i < 27; ++i) {
+        int px = VEL[i][0] + 1, py = VEL[i][1] + 1, pz = VEL[i][2] + 1;
+        double s = 0.0;
+        for (int m = 0; m < 27; ++m) s += X[px][m % 3] * Y[py][(m / 3) % 3] * Z[pz][m / 9] * kap[m];
+        f[i] = s;
+    }
+}
+
+/* Moment / cumulant conversion by the set-partition formulas, for the
+ * multiset of axes of index m (x a times, y b times, z c times, n <= 6):
+ *   cumulant = sum over partitions pi of (-1)^(|pi|-1) (|pi|-1)! prod_B mom(B)
+ *   moment   = sum over partitions pi of prod_B cum(B)
+ * where a block's value is that of its own axis multiset; blocks of one
+ * element are zero (zero mean), so those partitions are left out.  The
+ * partitions of each index are enumerated once (restricted growth strings)
+ * into a table when the library is loaded. */
+#define PART_MAX 64
+typedef struct {
+    int n_part;
+    int n_blk[PART_MAX];
+    int blk[PART_MAX][3];          /* at most 3 blocks of >= 2 elements among 6 */
+} part_table;
+static part_table PARTS[27];
+
+static void enumerate_partitions(int m, const int *axis, int n, int *label, int pos, int nblk) {
+    if (pos == n) {
+        int idx[6], size[6];
+        for (int b = 0; b < nblk; ++b) idx[b] = size[b] = 0;
+        for (int e = 0; e < n; ++e) {
+            static const int W[3] = {1, 3, 9};
+            idx[label[e]] += W[axis[e]];
+            ++size[label[e]];
+        }
+        for (int b = 0; b < nblk; ++b)
+            if (size[b] == 1) return;
+        part_table *t = &PARTS[m];
+        t->n_blk[t->n_part] = nblk;
+        for (int b = 0; b < nblk; ++b) t->blk[t->n_part][b] = idx[b];
+        ++t->n_part;
+        return;
+    }
+    for (int b = 0; b <= nblk; ++b) {
+        label[pos] = b;
+        enumerate_partitions(m, axis, n, label, pos + 1, b == nblk ? nblk + 1 : nblk);
+    }
+}
+
+__attribute__((constructor)) static void build_partition_tables(void) {
+    for (int m = 0; m < 27; ++m) {
+        int axis[6], label[6], n = 0;
+        int cnt[3] = {m % 3, (m / 3) % 3, m / 9};
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < cnt[a]; ++k) axis[n++] = a;
+        PARTS[m].n_part = 0;
+        if (n >= 2) enumerate_partitions(m, axis, n, label, 0, 0);
+    }
+}
+
+static double convert(int m, const double *val, int to_cumulant) {
+    const part_table *t = &PARTS[m];
+    double s = 0.0;
+    for (int q = 0; q < t->n_part; ++q) {
+        double prod = 1.0;
+        for (int b = 0; b < t->n_blk[q]; ++b) prod *= val[t->blk[q][b]];
+        if (to_cumulant) {
+            double fact = 1.0;
+            for (int k = 2; k < t->n_blk[q]; ++k) fact *= k;
+            prod *= ((t->n_blk[q] - 1) % 2 ? -1.0 : 1.0) * fact;
+        }
+        s += prod;
+    }
+    return s;
+}
+
+static int order_of(int m) { return m % 3 + (m / 3) % 3 + m / 9; }
+
+/* Normalised cumulants of orders >= 2 of f about the Guo velocity (orders 0
+ * and 1 returned as 0), for the tests. */
+void orc_cumulants(const orc_problem *p, const double *f, double *cum) {
+    double rho, u[3], kap[27], mom[27];
+    orc_moments(27, f, p->force, &rho, u);
+    orc_central_moments(f, u, kap);
+    for (int m = 0; m < 27; ++m) mom[m] = order_of(m) >= 2 ? kap[m] / rho : 0.0;
+    for (int m = 0; m < 27; ++m) cum[m] = order_of(m) >= 2 ? convert(m, mom, 1) : 0.0;
+}
+
+/* Second-order relaxation of the moment-indexed array v (index a + 3b +
+ * 9c): the normal entries v[2] (xx), v[6] (yy), v[18] (zz) as their trace,
+ * relaxed with wb towards 3 eq, and the differences xx - yy, xx - zz,
+ * relaxed with w towards 0; the off-diagonal v[4] (xy), v[10] (xz), v[12]
+ * (yz) with w towards 0. */
+static void relax_second(double *v, double eq, double w, double wb) {
+    const int XX = 2, YY = 6, ZZ = 18, XY = 4, XZ = 10, YZ = 12;
+    double T = v[XX] + v[YY] + v[ZZ], D1 = v[XX] - v[YY], D2 = v[XX] - v[ZZ];
+    T -= wb * (T - 3.0 * eq);
+    D1 *= 1.0 - w;
+    D2 *= 1.0 - w;
+    v[XX] = (T + D1 + D2) / 3.0;
+    v[YY] = (T - 2.0 * D1 + D2) / 3.0;
+    v[ZZ] = (T + D1 - 2.0 * D2) / 3.0;
+    v[XY] *= 1.0 - w;
+    v[XZ] *= 1.0 - w;
+    v[YZ] *= 1.0 - w;
+}
+
+static void collide_central(const orc_problem *p, const double *f, double *fs) {
+    double rho, u[3], kap[27];
+    orc_moments(27, f, p->force, &rho, u);
+    orc_central_moments(f, u, kap);
+    double w = p->omega_plus, wb = p->cm_bulk, wh = p->cm_high;
+    if (p->op == ORC_CM) {
+        relax_second(kap, rho / 3.0, w, wb);
+        for (int m = 0; m < 27; ++m) {
+            if (order_of(m) < 3) continue;
+            double eq = rho;
+            int cnt[3] = {m % 3, (m / 3) % 3, m / 9};
+            for (int a = 0; a < 3; ++a) eq *= cnt[a] == 0 ? 1.0 : (cnt[a] == 1 ? 0.0 : 1.0 / 3.0);
+            kap[m] -= wh * (kap[m] - eq);
+        }
+    } else {
+        double mom[27], cum[27], post[27];
+        for (int m = 0; m < 27; ++m) mom[m] = order_of(m) >= 2 ? kap[m] / rho : 0.0;
+        for (int m = 0; m < 27; ++m) cum[m] = order_of(m) >= 2 ? convert(m, mom, 1) : 0.0;
+        relax_second(cum, 1.0 / 3.0, w, wb);
+        for (int m = 0; m < 27; ++m)
+            if (order_of(m) >= 3) cum[m] *= 1.0 - wh;
+        for (int m = 0; m < 27; ++m) post[m] = order_of(m) >= 2 ? convert(m, cum, 0) : 0.0;
+        for (int m = 0; m < 27; ++m)
+            if (order_of(m) >= 2) kap[m] = rho * post[m];
+    }
+    kap[0] = rho;
+    kap[1] = 0.5 * p->force[0];
+    kap[3] = 0.5 * p->force[1];
+    kap[9] = 0.5 * p->force[2];
+    orc_from_central(kap, u, fs);
+}
+
 /* One cell's collision (Eq. 3 with Eq. 5, TRT or MRT): f -> fs. */
 void orc_collide(const orc_problem *p, const double *f, double *fs) {
     int q = p->q;
@@ -211,6 +415,10 @@ void orc_collide(const orc_problem *p, const double *f, double *fs) {
     orc_moments(q, f, p->force, &rho, u);
     orc_equilibrium(q, rho, u, feq);
     orc_guo_source(q, u, p->force, S);
+    if (p->op == ORC_CM || p->op == ORC_CUM) {
+        collide_central(p, f, fs);
+        return;
+    }
     if (p->op == ORC_MRT) {
         collide_mrt(p, f, feq, S, fs);
         return;
