@@ -370,16 +370,18 @@ def bench_pull(a, P, stream, peak, per32, pairs=10):
 
 def bench_operators(a, P, stream, peak, pairs=10):
     """Sec. 5.1's comparison of streaming patterns per collision operator:
-    AA and pull MFLUPS for SRT, TRT and MRT on the porosity-0.5 domain
-    (GB/s at each scheme's algorithmic bytes)."""
+    AA and pull MFLUPS for SRT, TRT and MRT (D3Q19) and SRT, TRT, central
+    moments and cumulants (D3Q27) on the porosity-0.5 domain (GB/s at each
+    scheme's algorithmic bytes)."""
     import torch
     phi = 0.5 if 0.5 in a.porosities else a.porosities[0]
     g = geometry_for(phi, a.size)
     res = []
-    for name, op in (("SRT", P.SRT), ("TRT", P.TRT), ("MRT", P.MRT)):
-        row = {"op": name}
-        for scheme, layout, idx in (("aa", P.SPARSE, (Q - 1) * B_IDX / 2), ("pull", P.SPARSE_PULL, (Q - 1) * B_IDX)):
-            d = P.Domain(g.flags, periodic=7, q=Q, op=op, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
+    for q, name, op in ((19, "SRT", P.SRT), (19, "TRT", P.TRT), (19, "MRT", P.MRT), (27, "SRT", P.SRT),
+                        (27, "TRT", P.TRT), (27, "CM", P.CM), (27, "CUMULANT", P.CUMULANT)):
+        row = {"op": name, "stencil": f"D3Q{q}"}
+        for scheme, layout, idx in (("aa", P.SPARSE, (q - 1) * B_IDX / 2), ("pull", P.SPARSE_PULL, (q - 1) * B_IDX)):
+            d = P.Domain(g.flags, periodic=7, q=q, op=op, omega=OMEGA, trt_magic=MAGIC, force=FORCE,
                          layout=layout, stream=stream)
             d.step(4)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -390,7 +392,7 @@ def bench_operators(a, P, stream, peak, pairs=10):
             ms = e0.elapsed_time(e1) / (2 * pairs)
             nf = d.n_fluid
             m = nf / (ms / 1e3) / 1e6
-            gbs = nf * (2 * Q * 4 + idx) / (ms / 1e3) / 1e9
+            gbs = nf * (2 * q * 4 + idx) / (ms / 1e3) / 1e9
             row[scheme] = {"mflups": round(m, 1), "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
             d.close()
         row["aa_over_pull"] = round(row["aa"]["mflups"] / row["pull"]["mflups"], 4)

@@ -64,7 +64,7 @@ typedef enum {
     SLBM_EDEVICE = 8        /* a device-side check latched an error (checked kernels) */
 } slbm_status;
 
-enum { SLBM_SRT = 0, SLBM_TRT = 1, SLBM_MRT = 2 };
+enum { SLBM_SRT = 0, SLBM_TRT = 1, SLBM_MRT = 2, SLBM_CM = 3, SLBM_CUMULANT = 4 };
 enum { SLBM_FP32 = 0, SLBM_FP16 = 1, SLBM_BF16 = 2 };
 enum { SLBM_LAYOUT_SPARSE = 0, SLBM_LAYOUT_DENSE = 1, SLBM_LAYOUT_SPARSE_PULL = 2 };
 enum { SLBM_MEM_DEVICE = 0, SLBM_MEM_HOST = 1 };
@@ -77,7 +77,8 @@ typedef struct {
     const uint8_t *flags;      /* HOST, nx*ny*nz flags (0..3), read during create only */
     uint32_t periodic;         /* bit0 x, bit1 y, bit2 z */
     int32_t q;                 /* 19 or 27 */
-    int32_t op;                /* SLBM_SRT, SLBM_TRT or SLBM_MRT (D3Q19, sparse and pull layouts) */
+    int32_t op;                /* SLBM_SRT, SLBM_TRT, SLBM_MRT (D3Q19), SLBM_CM or SLBM_CUMULANT
+                                  (D3Q27); MRT, CM and cumulant: sparse and pull layouts */
     double omega_plus;         /* 1/tau in (0, 2) (Eq. 7) */
     double trt_magic;          /* TRT magic parameter Lambda > 0; ignored for SRT */
     double force[3];           /* constant body-force density (Guo) */
@@ -107,6 +108,20 @@ typedef struct {
  * s_q = 1.2, s_m = 1.98; trt_magic is ignored.  Sparse (AA) and pull
  * layouts, launch variants 0 and 2 with at most 2 cells per thread; no
  * pools. */
+
+/* SLBM_CM, SLBM_CUMULANT -- central-moment and cumulant collisions (D3Q27
+ * only; the paper lists both among its generated operators, Sec. 4, and
+ * benchmarks them in Sec. 5.1; the cumulants are those of Geier et al.
+ * 2015).  Central moments are taken about the Guo velocity u = (j + F/2)/rho;
+ * the collision keeps rho, sets the first central moments to +F/2 (the
+ * momentum gains F), relaxes the trace of the second ones with the bulk rate
+ * towards 3 rho c_s^2 and their deviatoric part with omega_plus (the
+ * viscosity, Eq. 7), and the moments of order 3 to 6 with the higher rate:
+ * SLBM_CM towards the factorised D3Q27 equilibrium rho prod m(.), m = (1, 0,
+ * 1/3); SLBM_CUMULANT relaxes their cumulants (of kappa/rho) towards 0, with
+ * the higher rate fixed at 1.  Rates: bulk 1 and higher 1 until
+ * sparse_lbm_set_cm_rates says otherwise; trt_magic is ignored.  Launch
+ * variants 0 (both steps) and 2 (odd step, 1 or 2 cells); no pools. */
 
 /* SLBM_LAYOUT_SPARSE_PULL -- the two-grid pull scheme the paper compares the
  * AA pattern with (Sec. 5.1, Table 2's pull row): the same compacted cells and
@@ -264,6 +279,13 @@ slbm_status sparse_lbm_set_state(slbm_t *h, const void *host, int64_t step);
  * others must lie in (0, 2)).  The stress entries (9, 11, 13, 14, 15) set
  * the viscosity.  SLBM_EINVAL for non-MRT domains or rates out of range. */
 slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates);
+
+/* SLBM_CM and SLBM_CUMULANT domains: the relaxation rate of the trace of the
+ * second-order central moments (bulk viscosity) and of every moment of
+ * order 3 to 6, each in (0, 2].  Cumulant domains take higher == 1 only
+ * (SLBM_EUNSUPPORTED otherwise).  SLBM_EINVAL for other domains or rates out
+ * of range.  Cached graphs are dropped. */
+slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher);
 
 /* Launch shape used for a parity (0 even, 1 odd), chosen by the autotuner.
  * variant 0: `cells` cells per thread (even 1/2/4 consecutive cells; odd 1/2

@@ -11,7 +11,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libsparse_lbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EDIVERGED, ETIMEOUT, EABORTED, EDEVICE = range(9)
-SRT, TRT, MRT = 0, 1, 2
+SRT, TRT, MRT, CM, CUMULANT = 0, 1, 2, 3, 4
 FP32, FP16, BF16 = 0, 1, 2
 SPARSE, DENSE, SPARSE_PULL = 0, 1, 2
 ORDER_LEX, ORDER_BRICK8, ORDER_HYBRID = 0, 1, 2
@@ -71,6 +71,7 @@ SIGNATURES = {
     "sparse_lbm_set_state": (_st, [_vp, _vp, _i64]),
     "sparse_lbm_set_launch": (_st, [_vp, _i32, _i32, _i32, _i32]),
     "sparse_lbm_set_mrt_rates": (_st, [_vp, _vp]),
+    "sparse_lbm_set_cm_rates": (_st, [_vp, C.c_double, C.c_double]),
     "sparse_lbm_set_checked": (_st, [_vp, _i32]),
     "sparse_lbm_device_error": (_st, [_vp, C.POINTER(_i32)]),
     "sparse_lbm_free": (None, [_vp]),

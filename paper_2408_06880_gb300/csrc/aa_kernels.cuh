@@ -132,6 +132,7 @@ __device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideP
             F2 h[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i] = F2{make_float2(g[c][i], g[c + 1][i])};
+            static_assert(OP == OP_TRT || OP == OP_MRT, "paired collision: TRT and MRT");
             if constexpr (OP == OP_MRT) {
                 static_assert(Q == 19, "MRT is defined for D3Q19");
                 collide_mrt_v<SCALED>(h, p);

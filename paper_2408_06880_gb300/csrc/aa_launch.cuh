@@ -138,12 +138,12 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
     return e;
 }
 
-// MRT domains (D3Q19): the plain even kernel (1 or 2 cells per thread; variant
-// 2: the 2 cells collided in pairs) and
-// the odd kernel (1 or 2 cells, L2 index prefetch unless variant 0; checked
-// mode), with the MRT collision.
-template <int ST>
-static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
+// MRT (D3Q19), central-moment and cumulant (D3Q27) domains: the plain even
+// kernel (1 or 2 cells per thread; MRT variant 2: the 2 cells collided in
+// pairs) and the odd kernel (1 or 2 cells, L2 index prefetch unless variant 0;
+// checked mode), with the operator's collision.
+template <int Q, int ST, int OP>
+static cudaError_t launch_moment_op(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
@@ -151,9 +151,13 @@ static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
     const CollideParams p = d.collide_params();
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
-        if (sh.cells == 1) aa_even_kernel<19, ST, 1, OP_MRT><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p);
-        else if (sh.variant == 2) aa_even_kernel<19, ST, 2, OP_MRT, true><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
-        else aa_even_kernel<19, ST, 2, OP_MRT><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+        if (sh.cells == 1) aa_even_kernel<Q, ST, 1, OP><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p);
+        else if constexpr (OP == OP_MRT) {
+            if (sh.variant == 2) aa_even_kernel<Q, ST, 2, OP, true><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+            else aa_even_kernel<Q, ST, 2, OP><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+        } else {
+            aa_even_kernel<Q, ST, 2, OP><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+        }
         return cudaGetLastError();
     }
     const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
@@ -162,16 +166,16 @@ static cudaError_t launch_mrt(const Domain &d, int parity, cudaStream_t st) {
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const bool bc = nl > 0;
     if (d.checked) {
-        auto kc = bc ? aa_odd_kernel<19, ST, 1, true, true, false, false, OP_MRT>
-                     : aa_odd_kernel<19, ST, 1, false, true, false, false, OP_MRT>;
+        auto kc = bc ? aa_odd_kernel<Q, ST, 1, true, true, false, false, OP>
+                     : aa_odd_kernel<Q, ST, 1, false, true, false, false, OP>;
         kc<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0, nullptr, nullptr);
         return cudaGetLastError();
     }
     const int cells = sh.cells == 2 ? 2 : 1;
-    auto k = cells == 1 ? (bc ? aa_odd_kernel<19, ST, 1, true, false, false, false, OP_MRT>
-                              : aa_odd_kernel<19, ST, 1, false, false, false, false, OP_MRT>)
-                        : (bc ? aa_odd_kernel<19, ST, 2, true, false, false, false, OP_MRT>
-                              : aa_odd_kernel<19, ST, 2, false, false, false, false, OP_MRT>);
+    auto k = cells == 1 ? (bc ? aa_odd_kernel<Q, ST, 1, true, false, false, false, OP>
+                              : aa_odd_kernel<Q, ST, 1, false, false, false, false, OP>)
+                        : (bc ? aa_odd_kernel<Q, ST, 2, true, false, false, false, OP>
+                              : aa_odd_kernel<Q, ST, 2, false, false, false, false, OP>);
     const int32_t pf = sh.variant == 2 ? (int32_t)persistent_grid(k, sh.threads, INT32_MAX) : 0;
     k<<<grid(cells), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pf, nullptr, nullptr);
     return cudaGetLastError();
@@ -214,7 +218,11 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
     if (nf == 0) return cudaSuccess;
     if constexpr (Q == 19) {
-        if (d.op == SLBM_MRT) return launch_mrt<ST>(d, parity, st);
+        if (d.op == SLBM_MRT) return launch_moment_op<19, ST, OP_MRT>(d, parity, st);
+    }
+    if constexpr (Q == 27) {
+        if (d.op == SLBM_CM) return launch_moment_op<27, ST, OP_CM>(d, parity, st);
+        if (d.op == SLBM_CUMULANT) return launch_moment_op<27, ST, OP_CUM>(d, parity, st);
     }
     const LaunchShape sh = d.shape[parity];
     if (parity == 0 && sh.variant >= 2) return launch_even_packed<Q, ST>(d, sh, st);

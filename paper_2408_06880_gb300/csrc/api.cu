@@ -102,7 +102,9 @@ static void default_shapes(Domain &d) {
     d.shape[0] = LaunchShape{64, 2, 0};
     d.shape[1] = LaunchShape{128, 1, 2};
     if (d.layout == SLBM_LAYOUT_SPARSE && d.storage != SLBM_BF16) {
-        if (d.op != SLBM_MRT)
+        if (d.op == SLBM_CM || d.op == SLBM_CUMULANT)
+            d.shape[0] = LaunchShape{128, 1, 0};
+        else if (d.op != SLBM_MRT)
             d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
         else if (d.storage == SLBM_FP32)
             d.shape[0] = LaunchShape{64, 2, 2};
@@ -242,9 +244,12 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (N >= ((int64_t)1 << 31)) return err(SLBM_EUNSUPPORTED, "nx*ny*nz must be < 2^31");
     if (!s.flags) return err(SLBM_EINVAL, "flags must be non-NULL");
     if (s.q != 19 && s.q != 27) return err(SLBM_EINVAL, "q must be 19 or 27");
-    if (s.op != SLBM_SRT && s.op != SLBM_TRT && s.op != SLBM_MRT) return err(SLBM_EINVAL, "op must be SRT, TRT or MRT");
+    if (s.op < SLBM_SRT || s.op > SLBM_CUMULANT) return err(SLBM_EINVAL, "op must be SRT, TRT, MRT, CM or CUMULANT");
     if (s.op == SLBM_MRT && (s.q != 19 || s.layout == SLBM_LAYOUT_DENSE))
         return err(SLBM_EUNSUPPORTED, "MRT is built for D3Q19 sparse and pull layouts");
+    if ((s.op == SLBM_CM || s.op == SLBM_CUMULANT) && (s.q != 27 || s.layout == SLBM_LAYOUT_DENSE))
+        return err(SLBM_EUNSUPPORTED, "the central-moment and cumulant operators are built for D3Q27 sparse and pull "
+                                      "layouts");
     if (!(s.omega_plus > 0.0 && s.omega_plus < 2.0)) return err(SLBM_EINVAL, "omega_plus must lie in (0, 2)");
     if (s.op == SLBM_TRT && !(s.trt_magic > 0.0 && std::isfinite(s.trt_magic)))
         return err(SLBM_EINVAL, "trt_magic must be > 0");
@@ -299,6 +304,10 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     d.magic = s.trt_magic;
     d.omega_m = s.op == SLBM_TRT ? 1.0 / (s.trt_magic / (1.0 / s.omega_plus - 0.5) + 0.5) : s.omega_plus;
     if (d.op == SLBM_MRT) default_mrt_rates(d);
+    if (d.op == SLBM_CM || d.op == SLBM_CUMULANT) {   // bulk and higher-order rates
+        d.mrt_rates[0] = 1.0;
+        d.mrt_rates[1] = 1.0;
+    }
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
     default_shapes(d);
@@ -628,11 +637,29 @@ slbm_status sparse_lbm_set_mrt_rates(slbm_t *h, const double *rates) {
     return ok();
 }
 
+slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher) {
+    if (!h) return err(SLBM_EINVAL, "null handle");
+    Domain &d = h->d;
+    if (d.op != SLBM_CM && d.op != SLBM_CUMULANT) return err(SLBM_EINVAL, "not a central-moment or cumulant domain");
+    if (!(bulk > 0.0 && bulk <= 2.0) || !(higher > 0.0 && higher <= 2.0))
+        return err(SLBM_EINVAL, "rates must lie in (0, 2]");
+    if (d.op == SLBM_CUMULANT && higher != 1.0)
+        return err(SLBM_EUNSUPPORTED, "the cumulant collision is built with the higher-order rate 1");
+    d.mrt_rates[0] = bulk;
+    d.mrt_rates[1] = higher;
+    drop_graphs(d);
+    return ok();
+}
+
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
     if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
     if (h->d.op == SLBM_MRT && variant != 0 && variant != 2)
         return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
+    if ((h->d.op == SLBM_CM || h->d.op == SLBM_CUMULANT) && !(variant == 0 || (parity == 1 && variant == 2)))
+        return err(SLBM_EUNSUPPORTED, "central-moment and cumulant domains run variant 0 (and 2 for the odd step)");
+    if ((h->d.op == SLBM_CM || h->d.op == SLBM_CUMULANT) && parity == 0 && cells == 4)
+        return err(SLBM_EUNSUPPORTED, "central-moment and cumulant even step: 1 or 2 cells per thread");
     if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
         return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
     if (parity == 1 && h->d.order == SLBM_ORDER_HYBRID && h->d.layout == SLBM_LAYOUT_SPARSE &&

@@ -487,12 +487,22 @@ __device__ __forceinline__ Vel collide_mrt(float (&g)[19], const CollideParams &
 
 enum { OP_TRT = 0, OP_MRT = 1 };
 
-// The collision of operator OP (SRT is TRT with equal rates).
+}  // namespace slbm
+
+#include "central.cuh"
+
+namespace slbm {
+
+// The collision of operator OP (SRT is TRT with equal rates; OP_CM and
+// OP_CUM are the D3Q27 central-moment and cumulant collisions).
 template <int Q, bool SCALED, int OP>
 __device__ __forceinline__ Vel collide_op(float (&g)[Q], const CollideParams &p) {
     if constexpr (OP == OP_MRT) {
         static_assert(Q == 19, "MRT is defined for D3Q19");
         return collide_mrt<SCALED>(g, p);
+    } else if constexpr (OP == OP_CM || OP == OP_CUM) {
+        static_assert(Q == 27, "the central-moment operators are defined for D3Q27");
+        return collide_central<SCALED, OP>(g, p);
     } else {
         return collide<Q, SCALED>(g, p);
     }

@@ -713,7 +713,7 @@ slbm_status slbm_pool_add(slbm_pool_t *p, slbm_t *h, int32_t *slot) {
     if (!p || !h || !slot) return perr(SLBM_EINVAL, "null argument");
     const Domain &d = h->d;
     if (d.layout != SLBM_LAYOUT_SPARSE) return perr(SLBM_EUNSUPPORTED, "pool members must use the sparse layout");
-    if (d.op == SLBM_MRT) return perr(SLBM_EUNSUPPORTED, "pools step SRT/TRT members");
+    if (d.op != SLBM_SRT && d.op != SLBM_TRT) return perr(SLBM_EUNSUPPORTED, "pools step SRT/TRT members");
     if (d.q != p->q || d.storage != p->storage) return perr(SLBM_EINVAL, "member q / storage differ from the pool's");
     for (int32_t s = 0; s < p->capacity; ++s)
         if (p->members[s] == h) return perr(SLBM_EINVAL, "domain is already a member");

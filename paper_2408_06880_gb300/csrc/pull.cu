@@ -87,6 +87,10 @@ static cudaError_t launch_pull_st(const Domain &d, int64_t t, cudaStream_t st) {
     if constexpr (Q == 19) {
         if (d.op == SLBM_MRT) return launch_pull_op<Q, ST, OP_MRT>(d, t, st);
     }
+    if constexpr (Q == 27) {
+        if (d.op == SLBM_CM) return launch_pull_op<Q, ST, OP_CM>(d, t, st);
+        if (d.op == SLBM_CUMULANT) return launch_pull_op<Q, ST, OP_CUM>(d, t, st);
+    }
     return launch_pull_op<Q, ST, OP_TRT>(d, t, st);
 }
 

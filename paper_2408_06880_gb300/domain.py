@@ -165,6 +165,12 @@ class Domain:
         odd step: variant 2 L2 index prefetch, 3 re-read slots, 4 16-bit codes."""
         A.check(A.lib().sparse_lbm_set_launch(self.h, parity, threads, cells, variant))
 
+    def set_cm_rates(self, bulk: float = 1.0, higher: float = 1.0):
+        """Central-moment and cumulant domains: the rate of the trace of the
+        second-order central moments and of the moments of order 3..6
+        (cumulant domains: higher == 1)."""
+        A.check(A.lib().sparse_lbm_set_cm_rates(self.h, float(bulk), float(higher)))
+
     def set_mrt_rates(self, rates):
         """MRT domains: the 19 per-moment relaxation rates (basis order rho, e,
         eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx,

@@ -64,12 +64,15 @@ def size_class(n_fluid: int) -> int:
 def _valid(info: dict, parity: int, shape) -> bool:
     """Shapes the library accepts for this domain: no bulk-staged BF16 (even
     variants 1 and 3, odd variant 1); MRT runs variants 0 and 2 with at most
-    2 cells per thread."""
+    2 cells per thread; the central-moment and cumulant operators variant 0
+    (and 2 for the odd step) with at most 2."""
     staged = shape[2] == 1 or (parity == 0 and shape[2] == 3)
     if staged and info["storage"] == A.BF16:
         return False
     if info["op"] == A.MRT:
         return shape[2] in (0, 2) and shape[1] <= 2
+    if info["op"] in (A.CM, A.CUMULANT):
+        return shape[1] <= 2 and (shape[2] == 0 or (parity == 1 and shape[2] == 2))
     return True
 
 

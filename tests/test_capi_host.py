@@ -57,8 +57,8 @@ def _desc(capi, flags, **kw):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("nx", 0), ("q", 15), ("op", 3), ("omega_plus", 0.0), ("omega_plus", 2.0), ("storage", 3),
-    ("scale_exp", 41), ("layout", 3), ("order", 2), ("trt_magic", -1.0), ("rho_out", 0.0),
+    ("nx", 0), ("q", 15), ("op", 5), ("op", -1), ("omega_plus", 0.0), ("omega_plus", 2.0), ("storage", 3),
+    ("scale_exp", 41), ("layout", 3), ("order", 3), ("trt_magic", -1.0), ("rho_out", 0.0),
 ])
 def test_invalid_descriptors_are_rejected(capi, field, value):
     flags = np.zeros((4, 4, 4), np.uint8)
@@ -83,6 +83,13 @@ def test_bad_flags_and_inlet_count(capi):
     assert capi.lib().sparse_lbm_create(C.byref(d), None, None, C.byref(h)) == capi.EINVAL
     d = _desc(capi, flags, layout=capi.DENSE)
     assert capi.lib().sparse_lbm_create(C.byref(d), None, None, C.byref(h)) == capi.EUNSUPPORTED
+    # MRT is D3Q19 only, the central-moment and cumulant operators D3Q27 only
+    for q, op in ((27, capi.MRT), (19, capi.CM), (19, capi.CUMULANT)):
+        d = _desc(capi, np.zeros((4, 4, 4), np.uint8), q=q, op=op)
+        assert capi.lib().sparse_lbm_create(C.byref(d), None, None, C.byref(h)) == capi.EUNSUPPORTED
+    for op in (capi.CM, capi.CUMULANT):
+        d = _desc(capi, np.zeros((4, 4, 4), np.uint8), q=27, op=op, layout=capi.DENSE)
+        assert capi.lib().sparse_lbm_create(C.byref(d), None, None, C.byref(h)) == capi.EUNSUPPORTED
 
 
 def test_no_device_means_ecuda_not_fallback(capi):
