@@ -124,7 +124,7 @@ __device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
 // collision in the two lanes of the paired FP32 instructions -- the same
 // roundings per cell as the scalar pass, half the FP instructions.
 template <int Q, bool SCALED, int OP, int CPT, bool PACK>
-__device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideParams &p) {
+__device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideParams &p, Vel (&u)[CPT]) {
     if constexpr (PACK) {
         static_assert(CPT % 2 == 0, "paired collision: an even number of cells");
 #pragma unroll
@@ -133,12 +133,15 @@ __device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideP
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i] = F2{make_float2(g[c][i], g[c + 1][i])};
             static_assert(OP == OP_TRT || OP == OP_MRT, "paired collision: TRT and MRT");
+            VelT<F2> v;
             if constexpr (OP == OP_MRT) {
                 static_assert(Q == 19, "MRT is defined for D3Q19");
-                collide_mrt_v<SCALED>(h, p);
+                v = collide_mrt_v<SCALED>(h, p);
             } else {
-                collide_v<Q, SCALED>(h, p);
+                v = collide_v<Q, SCALED>(h, p);
             }
+            u[c] = Vel{v.x.v.x, v.y.v.x, v.z.v.x};
+            u[c + 1] = Vel{v.x.v.y, v.y.v.y, v.z.v.y};
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 g[c][i] = h[i].v.x;
@@ -147,17 +150,56 @@ __device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideP
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) collide_op<Q, SCALED, OP>(g[c], p);
+        for (int c = 0; c < CPT; ++c) u[c] = collide_op<Q, SCALED, OP>(g[c], p);
     }
 }
 
-template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false>
-__global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
-                                                      int32_t nf, CollideParams p) {
+template <int Q, bool SCALED, int OP, int CPT, bool PACK>
+__device__ __forceinline__ void collide_cells(float (&g)[CPT][Q], const CollideParams &p) {
+    Vel u[CPT];
+    collide_cells<Q, SCALED, OP, CPT, PACK>(g, p, u);
+}
+
+// Inlet/outlet links of the even step, applied by the even kernel itself.
+// The links are numbered by cell (link_cell ascending) and ltile[t] is the
+// first link of a cell at or after cell 32 t, so the links of the cells
+// [32 t0, 32 t1) are ltile[t0] .. ltile[t1] - 1.  A block reads its range
+// while its populations load; after its stores it writes its cells'
+// velocities to shared memory, synchronises, and its threads replace each
+// link slot (re-read after the barrier) by its map -- the operations of the
+// separate fix-up kernels.
+struct EvenLinks {
+    const int32_t *ltile, *link_cell, *link_dir;
+    const LinkMap *maps;
+};
+constexpr int EVEN_LINK_TILE = 32;
+
+// Link range [b0, b1) of the cells [kb, ke), kb a multiple of 32.
+__device__ __forceinline__ void even_link_range(const EvenLinks &lk, int32_t kb, int32_t ke, int32_t &b0,
+                                                int32_t &b1) {
+    b0 = lk.ltile[kb / EVEN_LINK_TILE];
+    b1 = lk.ltile[(ke + EVEN_LINK_TILE - 1) / EVEN_LINK_TILE];
+}
+
+template <int ST>
+__device__ __forceinline__ void even_links_apply(typename Store<ST>::T *pdf, int32_t S, int32_t kb, int32_t b0,
+                                                 int32_t b1, const float *us, int32_t span, const EvenLinks &lk,
+                                                 float scale) {
+    using St = Store<ST>;
+    for (int32_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+        const int32_t c = lk.link_cell[b] - kb;
+        const LinkMap m = lk.maps[b];
+        typename St::T *slot = pdf + lk.link_dir[b] * S + (kb + c);
+        *slot = St::pack(apply_link(m, St::raw(*slot), us[c], us[span + c], us[2 * span + c], scale));
+    }
+}
+
+// Load, collide and store the CPT cells k0 .. k0 + CPT - 1 of the even step.
+template <int Q, int ST, int CPT, int OP, bool PACK>
+__device__ __forceinline__ void aa_even_cells(typename Store<ST>::T *__restrict__ pdf, int32_t S, int32_t nf,
+                                              const CollideParams &p, int32_t k0, Vel (&u)[CPT]) {
     using St = Store<ST>;
     using T = typename St::T;
-    const int32_t k0 = (blockIdx.x * blockDim.x + threadIdx.x) * CPT;
-    if (k0 >= nf) return;
     float g[CPT][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -166,7 +208,7 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
 #pragma unroll
         for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
     }
-    collide_cells<Q, St::scaled, OP, CPT, PACK>(g, p);
+    collide_cells<Q, St::scaled, OP, CPT, PACK>(g, p, u);
     const bool full = k0 + CPT <= nf;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -182,6 +224,38 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
             for (int c = 0; c < CPT; ++c)
                 if (k0 + c < nf) dst[c] = y.v[c];
         }
+    }
+}
+
+// BC: the domain has inlet/outlet links; the kernel applies their maps to
+// the link slots it stored (EvenLinks; dynamic shared memory: 3 x blockDim x
+// CPT floats).
+template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false, bool BC = false>
+__global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
+                                                      int32_t nf, CollideParams p, EvenLinks lk = {}) {
+    const int32_t k0 = (blockIdx.x * blockDim.x + threadIdx.x) * CPT;
+    if constexpr (BC) {
+        extern __shared__ float even_us[];
+        const int32_t span = blockDim.x * CPT, kb = blockIdx.x * span;
+        const int32_t ke = kb + span < nf ? kb + span : nf;
+        int32_t b0, b1;
+        even_link_range(lk, kb, ke, b0, b1);
+        Vel u[CPT] = {};
+        if (k0 < nf) aa_even_cells<Q, ST, CPT, OP, PACK>(pdf, S, nf, p, k0, u);
+        if (b0 == b1) return;                         // uniform across the block
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int32_t l = threadIdx.x * CPT + c;
+            even_us[l] = u[c].x;
+            even_us[span + l] = u[c].y;
+            even_us[2 * span + l] = u[c].z;
+        }
+        __syncthreads();
+        even_links_apply<ST>(pdf, S, kb, b0, b1, even_us, span, lk, p.scale);
+    } else {
+        if (k0 >= nf) return;
+        Vel u[CPT];
+        aa_even_cells<Q, ST, CPT, OP, PACK>(pdf, S, nf, p, k0, u);
     }
 }
 
@@ -375,10 +449,12 @@ namespace slbm {
 constexpr int32_t ERR_STAGE_TIMEOUT = 100;
 
 // ---------------------------------------------------------------------------
-// Boundary fix-up around the even step (domains with inlet/outlet links).
-// The even step stays cell-local and index-free; before it, each boundary
-// cell's velocity at the current time is saved; after it, the values the even
-// step stored in the cell's link slots are replaced by their link maps.
+// Boundary fix-up around the even step of a pool member with inlet/outlet
+// links (the pool kernels do not apply link maps).  Before the even step each
+// boundary cell's Guo velocity at the current time is saved, with the TRT
+// collision's bits; after it, the values the even step stored in the cell's
+// link slots are replaced by their link maps -- the same operations as the
+// even kernels that fold the maps in (EvenLinks), so both give the same bits.
 template <int Q, int ST>
 __global__ void bc_pre_kernel(const typename Store<ST>::T *__restrict__ pdf, int32_t S,
                               const int32_t *__restrict__ bcell, int32_t n_bcells, CollideParams p,
@@ -389,13 +465,11 @@ __global__ void bc_pre_kernel(const typename Store<ST>::T *__restrict__ pdf, int
     const int32_t k = bcell[j];
     float g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = St::ld(pdf[i * S + k], p.inv_scale);
-    float drho, jx, jy, jz;
-    moments<Q>(g, drho, jx, jy, jz);
-    const float rho = 1.0f + drho;
-    ubuf[3 * j] = (jx + 0.5f * p.fx) / rho;
-    ubuf[3 * j + 1] = (jy + 0.5f * p.fy) / rho;
-    ubuf[3 * j + 2] = (jz + 0.5f * p.fz) / rho;
+    for (int i = 0; i < Q; ++i) g[i] = St::raw(pdf[i * S + k]);
+    const Vel u = guo_velocity<Q, St::scaled>(g, p);
+    ubuf[3 * j] = u.x;
+    ubuf[3 * j + 1] = u.y;
+    ubuf[3 * j + 2] = u.z;
 }
 
 template <int ST>
@@ -512,15 +586,19 @@ __global__ void __launch_bounds__(TILE) aa_odd_staged_kernel(typename Store<ST>:
 }
 
 // TILE cells per tile, CPT consecutive cells per thread (TILE / CPT threads);
-// PACK: the cells of a thread collide in pairs (collide_cells).
-template <int Q, int ST, int TILE, int NSTAGE, int CPT = 1, bool PACK = false>
+// PACK: the cells of a thread collide in pairs (collide_cells).  BC: the
+// inlet/outlet link maps of a tile's cells are applied after its stores
+// (EvenLinks), behind one barrier.
+template <int Q, int ST, int TILE, int NSTAGE, int CPT = 1, bool PACK = false, bool BC = false>
 __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Store<ST>::T *__restrict__ pdf,
                                                                     int32_t S, int32_t nf, CollideParams p,
-                                                                    int32_t *err) {
+                                                                    int32_t *err, EvenLinks lk = {}) {
     using St = Store<ST>;
     using T = typename St::T;
+    static_assert(TILE % EVEN_LINK_TILE == 0, "tiles of whole link tiles");
     __shared__ __align__(128) T tile[NSTAGE][Q][TILE];
     __shared__ __align__(8) uint64_t bar[NSTAGE];
+    __shared__ float us[BC ? 3 * TILE : 1];
     const int tid = threadIdx.x;
     const int32_t n_tiles = S / TILE;
     StageState ss;
@@ -547,6 +625,8 @@ __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Sto
     for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
         const int s = it % NSTAGE;
         const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+        int32_t b0 = 0, b1 = 0;
+        if constexpr (BC) even_link_range(lk, t * TILE, (t + 1) * TILE < nf ? (t + 1) * TILE : nf, b0, b1);
         const bool ok = mbar_wait_bounded(&bar[s], ph);
         float g[CPT][Q];
         if (ok) {
@@ -569,8 +649,9 @@ __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Sto
             if (tn < n_tiles) issue(tn, s);
         }
         const int32_t k0 = t * TILE + CPT * tid;
+        Vel u[CPT] = {};
         if (k0 < nf) {
-            collide_cells<Q, St::scaled, OP_TRT, CPT, PACK>(g, p);
+            collide_cells<Q, St::scaled, OP_TRT, CPT, PACK>(g, p, u);
             const bool full = k0 + CPT <= nf;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -586,6 +667,19 @@ __global__ void __launch_bounds__(TILE / CPT) aa_even_staged_kernel(typename Sto
                     for (int c = 0; c < CPT; ++c)
                         if (k0 + c < nf) dst[c] = y.v[c];
                 }
+            }
+        }
+        if constexpr (BC) {
+            if (b0 != b1) {                    // uniform across the block
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    us[CPT * tid + c] = u[c].x;
+                    us[TILE + CPT * tid + c] = u[c].y;
+                    us[2 * TILE + CPT * tid + c] = u[c].z;
+                }
+                __syncthreads();
+                // the next write of us follows the next tile's barrier
+                even_links_apply<ST>(pdf, S, t * TILE, b0, b1, us, TILE, lk, p.scale);
             }
         }
     }

@@ -11,6 +11,12 @@
 
 namespace slbm {
 
+// Link tables of a domain for the even kernels that apply the link maps.
+static EvenLinks even_links_of(const Domain &d) {
+    return EvenLinks{(const int32_t *)d.ltile.p, (const int32_t *)d.link_cell.p, (const int32_t *)d.link_dir.p,
+                     (const LinkMap *)d.link_map.p};
+}
+
 // Persistent grid: SMs x resident CTAs of this kernel at this block size and
 // dynamic shared memory on the current device (looked up once each).
 template <class K>
@@ -45,12 +51,16 @@ static cudaError_t launch_staged(const Domain &d, int parity, cudaStream_t st) {
     int32_t *err = reinterpret_cast<int32_t *>(d.err.p);
     const int64_t tiles = S / TILE;
     if (parity == 0) {
+        const bool bc = d.n_links > 0;
+        const EvenLinks lk = bc ? even_links_of(d) : EvenLinks{};
         if constexpr (ST == ST_F16 || PACK) {    // 2 cells per thread (FP16: paired conversions)
-            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2, PACK>;
-            k<<<persistent_grid(k, TILE / 2, tiles), TILE / 2, 0, st>>>(pdf, S, nf, p, err);
+            auto k = bc ? aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2, PACK, true>
+                        : aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 2, PACK, false>;
+            k<<<persistent_grid(k, TILE / 2, tiles), TILE / 2, 0, st>>>(pdf, S, nf, p, err, lk);
         } else {
-            auto k = aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 1>;
-            k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err);
+            auto k = bc ? aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 1, false, true>
+                        : aa_even_staged_kernel<Q, ST, TILE, NSTAGE, 1, false, false>;
+            k<<<persistent_grid(k, TILE, tiles), TILE, 0, st>>>(pdf, S, nf, p, err, lk);
         }
     } else if constexpr (!PACK) {
         const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
@@ -104,7 +114,8 @@ static cudaError_t launch_window(const Domain &d, int nstage, cudaStream_t st) {
     }
 }
 
-// Boundary fix-up launches around the even step of a domain with links.
+// Boundary fix-up launches around a pool's even step for a member with links
+// (every even kernel of a domain of its own applies the link maps itself).
 template <int Q, int ST>
 cudaError_t launch_bc_pre(const Domain &d, cudaStream_t st) {
     const int32_t nb = (int32_t)d.n_bcells;
@@ -126,16 +137,21 @@ cudaError_t launch_bc_post(const Domain &d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int Q, int ST>
-static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st);
-
-template <int Q, int ST>
-static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
-    if (parity != 0 || d.n_bcells == 0) return launch_aa_storage_core<Q, ST>(d, parity, st);
-    cudaError_t e = launch_bc_pre<Q, ST>(d, st);
-    if (e == cudaSuccess) e = launch_aa_storage_core<Q, ST>(d, parity, st);
-    if (e == cudaSuccess) e = launch_bc_post<Q, ST>(d, st);
-    return e;
+// The plain even kernel, `threads` x CPT cells a block, with the link maps
+// folded in when the domain has inlet/outlet links.
+template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false>
+static cudaError_t launch_even_plain(const Domain &d, int threads, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    T *pdf = reinterpret_cast<T *>(d.pdf.p);
+    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
+    const CollideParams p = d.collide_params();
+    const dim3 grid((unsigned)((nf + threads * CPT - 1) / (threads * CPT)));
+    if (d.n_bcells > 0)
+        aa_even_kernel<Q, ST, CPT, OP, PACK, true><<<grid, threads, 3 * threads * CPT * sizeof(float), st>>>(
+            pdf, S, nf, p, even_links_of(d));
+    else
+        aa_even_kernel<Q, ST, CPT, OP, PACK, false><<<grid, threads, 0, st>>>(pdf, S, nf, p);
+    return cudaGetLastError();
 }
 
 // MRT (D3Q19), central-moment and cumulant (D3Q27) domains: the plain even
@@ -151,14 +167,11 @@ static cudaError_t launch_moment_op(const Domain &d, int parity, cudaStream_t st
     const CollideParams p = d.collide_params();
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
-        if (sh.cells == 1) aa_even_kernel<Q, ST, 1, OP><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p);
-        else if constexpr (OP == OP_MRT) {
-            if (sh.variant == 2) aa_even_kernel<Q, ST, 2, OP, true><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
-            else aa_even_kernel<Q, ST, 2, OP><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
-        } else {
-            aa_even_kernel<Q, ST, 2, OP><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p);
+        if (sh.cells == 1) return launch_even_plain<Q, ST, 1, OP>(d, sh.threads, st);
+        if constexpr (OP == OP_MRT) {
+            if (sh.variant == 2) return launch_even_plain<Q, ST, 2, OP, true>(d, sh.threads, st);
         }
-        return cudaGetLastError();
+        return launch_even_plain<Q, ST, 2, OP>(d, sh.threads, st);
     }
     const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
     const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);
@@ -197,22 +210,15 @@ static cudaError_t launch_even_packed(const Domain &d, const LaunchShape &sh, cu
             }
         }
     }
-    using T = typename Store<ST>::T;
-    T *pdf = reinterpret_cast<T *>(d.pdf.p);
-    const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
-    const CollideParams p = d.collide_params();
-    const unsigned span = (unsigned)(sh.threads * sh.cells);
-    const dim3 grid((unsigned)((nf + span - 1) / span));
     switch (sh.cells) {
-        case 2: aa_even_kernel<Q, ST, 2, OP_TRT, true><<<grid, sh.threads, 0, st>>>(pdf, S, nf, p); break;
-        case 4: aa_even_kernel<Q, ST, 4, OP_TRT, true><<<grid, sh.threads, 0, st>>>(pdf, S, nf, p); break;
+        case 2: return launch_even_plain<Q, ST, 2, OP_TRT, true>(d, sh.threads, st);
+        case 4: return launch_even_plain<Q, ST, 4, OP_TRT, true>(d, sh.threads, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <int Q, int ST>
-static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStream_t st) {
+static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
@@ -241,12 +247,11 @@ static cudaError_t launch_aa_storage_core(const Domain &d, int parity, cudaStrea
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
         switch (sh.cells) {
-            case 1: aa_even_kernel<Q, ST, 1><<<grid(1), sh.threads, 0, st>>>(pdf, S, nf, p); break;
-            case 2: aa_even_kernel<Q, ST, 2><<<grid(2), sh.threads, 0, st>>>(pdf, S, nf, p); break;
-            case 4: aa_even_kernel<Q, ST, 4><<<grid(4), sh.threads, 0, st>>>(pdf, S, nf, p); break;
+            case 1: return launch_even_plain<Q, ST, 1>(d, sh.threads, st);
+            case 2: return launch_even_plain<Q, ST, 2>(d, sh.threads, st);
+            case 4: return launch_even_plain<Q, ST, 4>(d, sh.threads, st);
             default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
     const int32_t *P = reinterpret_cast<const int32_t *>(d.P.p);
     const LinkMap *maps = reinterpret_cast<const LinkMap *>(d.link_map.p);

@@ -178,8 +178,8 @@ static void drop_graphs(Domain &d) {
 static void release_all(Domain &d) {
     Ctx cx = d.ctx();
     DevBuf *bufs[] = {&d.pdf,  &d.pdf2,   &d.P,         &d.code,      &d.code_base, &d.win_tab, &d.win_code, &d.face, &d.cell_voxel, &d.link_cell,
-                      &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.mask,
-                      &d.red_partial, &d.red_out, &d.err};
+                      &d.link_dir, &d.link_type, &d.link_map, &d.bcell, &d.bfirst, &d.bc_ubuf, &d.ltile,
+                      &d.mask, &d.red_partial, &d.red_out, &d.err};
     for (DevBuf *b : bufs) cx.release(*b);
 }
 

@@ -231,16 +231,22 @@ __device__ __forceinline__ F2 vrcp(F2 x) { return F2{make_float2(1.0f / x.v.x, 1
 // fma is one rounding; compiled without FMA contraction the sequence of
 // roundings is fixed, so every kernel gives the same bits for a cell.
 // V = float: one cell; V = F2: two cells, the same operations lane-wise.
+// Pair sums s_m = g_i + g_inv, d_m = g_i - g_inv (i = 2m + 1), the density
+// deviation drho, rho and the Guo velocity u = (j + F/2) / rho of shifted
+// populations in stored units, in the order of roundings of the TRT
+// collision (which calls it), so that a kernel that needs only u gets the
+// collision's bits.
 template <int Q, bool SCALED, class V>
-__device__ __forceinline__ VelT<V> collide_v(V (&g)[Q], const CollideParams &p) {
+__device__ __forceinline__ void pair_moments(const V (&g)[Q], V (&s)[(Q - 1) / 2], V (&d)[(Q - 1) / 2],
+                                             const CollideParams &p, V &drho, V &rho, VelT<V> &u) {
     constexpr int NP = (Q - 1) / 2;
-    V s[NP], d[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         s[m] = g[2 * m + 1] + g[2 * m + 2];
         d[m] = g[2 * m + 1] - g[2 * m + 2];
     }
-    V drho = g[0], jx = bc<V>(0.f), jy = bc<V>(0.f), jz = bc<V>(0.f);
+    V jx = bc<V>(0.f), jy = bc<V>(0.f), jz = bc<V>(0.f);
+    drho = g[0];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         drho = drho + s[m];
@@ -259,11 +265,29 @@ __device__ __forceinline__ VelT<V> collide_v(V (&g)[Q], const CollideParams &p) 
         jy = jy * is;
         jz = jz * is;
     }
-    const V rho = bc<V>(1.0f) + drho;
+    rho = bc<V>(1.0f) + drho;
     const V ir = vrcp(rho);
-    const V ux = vfma(bc<V>(0.5f), bc<V>(p.fx), jx) * ir;
-    const V uy = vfma(bc<V>(0.5f), bc<V>(p.fy), jy) * ir;
-    const V uz = vfma(bc<V>(0.5f), bc<V>(p.fz), jz) * ir;
+    u.x = vfma(bc<V>(0.5f), bc<V>(p.fx), jx) * ir;
+    u.y = vfma(bc<V>(0.5f), bc<V>(p.fy), jy) * ir;
+    u.z = vfma(bc<V>(0.5f), bc<V>(p.fz), jz) * ir;
+}
+
+// The Guo velocity of one cell with the TRT collision's bits.
+template <int Q, bool SCALED>
+__device__ __forceinline__ Vel guo_velocity(const float (&g)[Q], const CollideParams &p) {
+    float s[(Q - 1) / 2], d[(Q - 1) / 2], drho, rho;
+    Vel u;
+    pair_moments<Q, SCALED, float>(g, s, d, p, drho, rho, u);
+    return u;
+}
+
+template <int Q, bool SCALED, class V>
+__device__ __forceinline__ VelT<V> collide_v(V (&g)[Q], const CollideParams &p) {
+    constexpr int NP = (Q - 1) / 2;
+    V s[NP], d[NP], drho, rho;
+    VelT<V> u0;
+    pair_moments<Q, SCALED, V>(g, s, d, p, drho, rho, u0);
+    const V ux = u0.x, uy = u0.y, uz = u0.z;
     const V usq = vfma(uz, uz, vfma(uy, uy, ux * ux));
     const V uF = vfma(uz, bc<V>(p.fz), vfma(uy, bc<V>(p.fy), ux * bc<V>(p.fx)));
     const V E = vfma(bc<V>(-1.5f) * rho, usq, drho);            // drho - 1.5 rho u.u

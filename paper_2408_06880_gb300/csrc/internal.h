@@ -78,6 +78,7 @@ struct Domain {
     DevBuf cell_voxel;                 // N_F voxel ids (sparse)
     DevBuf link_cell, link_dir, link_type, link_map;   // boundary links (sparse)
     DevBuf bcell, bfirst, bc_ubuf;     // cells with links: id, first link (n+1), saved velocity
+    DevBuf ltile;                      // first link of each 32-cell tile (n_tiles + 1)
     int64_t n_bcells = 0;
     DevBuf mask;                       // per-voxel link mask (dense)
     DevBuf red_partial;                // per-chunk FP64 partial sums (5 doubles), then per-chunk maxima (2 floats)

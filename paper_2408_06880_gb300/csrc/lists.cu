@@ -236,6 +236,18 @@ struct BoundaryCells {             // first link of each cell that has links
     }
 };
 
+// ltile[t] = the first link b with link_cell[b] >= 32 t (link_cell is
+// ascending), t = 0 .. n_tiles: thread b fills the tiles after the previous
+// link's cell up to its own.
+__global__ void link_tiles_kernel(const int32_t *__restrict__ link_cell, int32_t n_links, int32_t n_tiles,
+                                  int32_t *__restrict__ ltile) {
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > n_links) return;
+    const int32_t lo = b == 0 ? 0 : link_cell[b - 1] / EVEN_LINK_TILE + 1;
+    const int32_t hi = b == n_links ? n_tiles : link_cell[b] / EVEN_LINK_TILE;
+    for (int32_t t = lo; t <= hi; ++t) ltile[t] = b;
+}
+
 struct CountScan {                 // exclusive offsets of per-cell link counts
     const uint8_t *count;
     int32_t *offset;
@@ -524,7 +536,15 @@ int build_sparse_lists(Ctx &cx, Domain &d, const uint8_t *d_flags, bool has_bc, 
         const int32_t end = (int32_t)n_links;
         if (cx.check(cudaMemcpyAsync((int32_t *)d.bfirst.p + nb, &end, 4, cudaMemcpyHostToDevice, cx.stream),
                      "bfirst end") ||
-            cx.alloc(d.bc_ubuf, nb * 3 * sizeof(float)) ||
+            cx.alloc(d.bc_ubuf, nb * 3 * sizeof(float)))
+            return -1;
+        // first link of each 32-cell tile, for the even kernels that apply
+        // the link maps themselves
+        const int32_t n_tiles = (int32_t)((d.n_fluid + EVEN_LINK_TILE - 1) / EVEN_LINK_TILE);
+        if (cx.alloc(d.ltile, ((int64_t)n_tiles + 1) * 4)) return -1;
+        link_tiles_kernel<<<(unsigned)((n_links + 1 + 255) / 256), 256, 0, cx.stream>>>(
+            (const int32_t *)d.link_cell.p, (int32_t)n_links, n_tiles, (int32_t *)d.ltile.p);
+        if (cx.check(cudaGetLastError(), "link_tiles launch") ||
             cx.check(cudaStreamSynchronize(cx.stream), "boundary cells"))
             return -1;
     }
