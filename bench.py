@@ -270,6 +270,7 @@ def run_ours(a, rank, world):
         out["pull"] = bench_pull(a, P, stream, peak, per)
         out["operators"] = bench_operators(a, P, stream, peak)
         out["fp16"] = bench_storage(a, P, stream, P.FP16, per)
+        out["accuracy"] = bench_accuracy(P, stream)
         out["e2e"] = bench_e2e(a, P)
         if world == 1:
             out["cpu_baseline"] = cpu_baseline(a, [g for _, g, _ in doms])
@@ -398,6 +399,32 @@ def bench_operators(a, P, stream, peak, pairs=10):
         row["aa_over_pull"] = round(row["aa"]["mflups"] / row["pull"]["mflups"], 4)
         res.append(row)
     return {"porosity": phi, "rows": res}
+
+
+def bench_accuracy(P, stream):
+    """Error of each PDF storage against the FP64 oracle, from its stored
+    values (tests/golden/packing32_srt_200.npz, written by the oracle-only
+    fixture script): the 32^3 relaxed packing, D3Q19 SRT, F = 1e-6 x, 200
+    steps from rest -- velocity relative L2 over all fluid cells and the
+    relative error of the permeability nu <u_x> / F_x."""
+    import geometry as G
+    fx = np.load(os.path.join(ROOT, "tests", "golden", "packing32_srt_200.npz"))
+    u_o = fx["u"]
+    k_o = float(fx["nu"]) * float(np.mean(u_o[:, 0])) / float(fx["force_x"])
+    g = G.relaxed_spheres()
+    out = {"workload": "32^3 relaxed packing (porosity 0.5), D3Q19 SRT, F = 1e-6 x, 200 steps from rest",
+           "reference": "FP64 oracle, stored values"}
+    for name, storage in (("fp32", P.FP32), ("fp16", P.FP16), ("bf16", P.BF16)):
+        d = P.Domain(g.flags, periodic=7, q=19, op=P.SRT, omega=1.25, force=(1e-6, 0.0, 0.0), storage=storage,
+                     scale_exp=P.auto_scale_exp(1e-3) if storage != P.FP32 else 0, stream=stream)
+        d.step(int(fx["steps"]))
+        _, u = d.macroscopic(P.ORDER_CELLS)
+        u = u.T.astype(np.float64)
+        d.close()
+        k = float(fx["nu"]) * float(np.mean(u[:, 0])) / float(fx["force_x"])
+        out[name] = {"u_rel_l2": float(f"{np.linalg.norm(u - u_o) / np.linalg.norm(u_o):.3g}"),
+                     "permeability_rel_err": float(f"{abs(k / k_o - 1):.3g}")}
+    return out
 
 
 def bench_storage(a, P, stream, storage, per32, pairs=20):
@@ -775,6 +802,10 @@ def run_workloads(a, pairs=10):
                      inlet_u=g.inlet_u if flags is None else None, rho_out=g.rho_out, q=q, op=P.TRT, omega=OMEGA,
                      trt_magic=MAGIC, storage=storage, scale_exp=P.auto_scale_exp(0.06) if storage else 0,
                      layout=layout, stream=stream, cell_order=order)
+        shapes = None
+        if layout == P.SPARSE and order != P.ORDER_HYBRID:
+            from paper_2408_06880_gb300 import tuner
+            shapes = tuner.tune_domain(d, reps=5, use_cache=False, stream=stream)   # state restored
         ms = _time_pairs(P, d, stream, pairs)
         nf = int(np.count_nonzero(g.flags == 0))
         per = (2 * q * b + (q - 1) * B_IDX / 2) if layout == P.SPARSE else None
@@ -793,6 +824,8 @@ def run_workloads(a, pairs=10):
              "n_fluid": nf, "fluid_fraction": round(nf / g.flags.size, 5),
              "mflups": round(nf / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
              "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)}
+        if shapes:
+            r["shapes"] = {"even": list(shapes["even"]), "odd": list(shapes["odd"]), "by": "autotuner"}
         if per is not None:
             gbs = nf * per / (ms / 1e3) / 1e9
             r.update({"gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})

@@ -121,7 +121,15 @@ def tune_domain(dom, reps: int = 9, use_cache: bool = True, stream=None) -> dict
         state, step = dom.get_state()
         for parity, key in todo:
             shapes = EVEN_SHAPES if parity == 0 else ODD_SHAPES
-            res = {s: _time_parity(dom, parity, s, reps, st) for s in shapes if _valid(info, parity, s)}
+            res = {}
+            for s in shapes:
+                if not _valid(info, parity, s):
+                    continue
+                try:
+                    res[s] = _time_parity(dom, parity, s, reps, st)
+                except A.SlbmError as e:          # a shape this domain refuses (cell order, layout)
+                    if e.status not in (A.EINVAL, A.EUNSUPPORTED):
+                        raise
             best = min(res, key=res.get)
             chosen[parity] = best
             cache[key] = {"shape": list(best), "ms": res[best],

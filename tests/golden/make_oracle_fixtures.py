@@ -7,6 +7,7 @@ library.  The oracle is compiled without FMA contraction and uses only IEEE
     python tests/golden/make_oracle_fixtures.py sweep     # sweep256_phi05_trt_1000.npz
     python tests/golden/make_oracle_fixtures.py bed       # bed_full_q27_200.npz
     python tests/golden/make_oracle_fixtures.py serving   # serving16_oracle.json
+    python tests/golden/make_oracle_fixtures.py packing   # packing32_srt_200.npz
 
 sweep: the 256^3 periodic Boolean packing of porosity 0.5 (seed 12), D3Q19
   TRT (omega+ = 1.25, magic 3/16), body force 1e-6 along x, rest start, 1000
@@ -22,6 +23,9 @@ serving: the first 16 requests of the permeability stream whose edge is 64 or
   1e-6 (the serving criterion) and then 1000 steps further, or 20000 steps;
   plus each request's voxel count, fluid cells and nu, so that the
   permeability at any of those steps is nu * (sum u_x / N) / F_x.
+packing: the 32^3 relaxed packing (r = 4, porosity 0.5, seed 1), D3Q19 SRT
+  (omega = 1.25), body force 1e-6 along x, rest start, 200 steps; stored:
+  rho and u of every fluid cell in the compacted lexicographic order, and nu.
 """
 from __future__ import annotations
 
@@ -119,7 +123,18 @@ def serving(tol=1e-6, max_steps=20000, chunk=100, after=1000):
             json.dump(out, fh)
 
 
+def packing():
+    g = G.relaxed_spheres()
+    p = O.Problem.from_geometry(g, q=19, op=O.SRT, omega_plus=1.25, force=(1e-6, 0.0, 0.0))
+    L = O.pull_list(p)
+    f = O.sparse_run(p, L, O.sparse_rest(p, L), 200)
+    rho, u = O.sparse_macroscopic(p, L, f)
+    path = os.path.join(HERE, "packing32_srt_200.npz")
+    np.savez_compressed(path, rho=rho, u=u, nu=np.float64(p.nu), steps=np.int64(200), force_x=np.float64(1e-6))
+    print(f"wrote {path}: N_F={L.n_fluid}", flush=True)
+
+
 if __name__ == "__main__":
-    what = sys.argv[1:] or ["sweep", "bed", "serving"]
+    what = sys.argv[1:] or ["sweep", "bed", "serving", "packing"]
     for w in what:
-        {"sweep": sweep, "bed": bed, "serving": serving}[w]()
+        {"sweep": sweep, "bed": bed, "serving": serving, "packing": packing}[w]()

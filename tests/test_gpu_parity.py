@@ -221,7 +221,7 @@ def test_window_staged_odd_step_over_many_tiles(case, stages):
 def test_window_staged_shape_refusals():
     g = G.boolean_spheres(16, 0.5, 2)
     with gpu_domain(g, q=19, op=P.TRT) as d:
-        for bad in ((64, 2, 6), (128, 1, 6), (128, 5, 6)):
+        for bad in ((64, 2, 6), (128, 1, 6), (128, 5, 6), (128, 1, 7)):
             with pytest.raises(P.SlbmError):
                 d.set_launch(1, *bad)
         with pytest.raises(P.SlbmError):

@@ -267,3 +267,10 @@ def test_stored_oracle_fixtures_match_their_recipes():
     f = O.sparse_run(p, L, O.sparse_rest(p, L), 100)
     _, u = O.sparse_macroscopic(p, L, f)
     assert float(np.sum(u[:, 0])) == o["sum_ux"][0]
+    # the packing fixture (the storage-accuracy report) is the oracle's run, bit for bit
+    fx = np.load(os.path.join(here, "packing32_srt_200.npz"))
+    g = G.relaxed_spheres()
+    p = O.Problem.from_geometry(g, q=19, op=O.SRT, omega_plus=1.25, force=(1e-6, 0.0, 0.0))
+    L = O.pull_list(p)
+    rho, u = O.sparse_macroscopic(p, L, O.sparse_run(p, L, O.sparse_rest(p, L), int(fx["steps"])))
+    assert np.array_equal(fx["rho"], rho) and np.array_equal(fx["u"], u) and float(fx["nu"]) == p.nu
