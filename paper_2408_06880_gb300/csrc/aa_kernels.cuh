@@ -174,9 +174,15 @@ struct EvenLinks {
 };
 constexpr int EVEN_LINK_TILE = 32;
 
-// Link range [b0, b1) of the cells [kb, ke), kb a multiple of 32.
+// Link range [b0, b1) of the cells [kb, ke), kb a multiple of 32 and
+// ke <= N_F; empty when kb >= ke (a staged tile of padding columns only),
+// without reading the table, whose last entry is tile ceil(N_F / 32).
 __device__ __forceinline__ void even_link_range(const EvenLinks &lk, int32_t kb, int32_t ke, int32_t &b0,
                                                 int32_t &b1) {
+    if (kb >= ke) {
+        b0 = b1 = 0;
+        return;
+    }
     b0 = lk.ltile[kb / EVEN_LINK_TILE];
     b1 = lk.ltile[(ke + EVEN_LINK_TILE - 1) / EVEN_LINK_TILE];
 }

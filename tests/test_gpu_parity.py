@@ -186,6 +186,41 @@ def test_launch_shapes_are_bitwise_identical(shape, q, storage):
     assert np.array_equal(got, want)
 
 
+def _mixed_bc_residue(residue, seed=13, shape=(40, 33, 29)):
+    """_mixed_bc with the last fluid voxels turned to walls until N_F mod 128
+    equals `residue`: the 64-cell tiles of the padded PDF-list then end in a
+    tile of padding columns only (residue <= 64), whose link range must stay
+    empty without reading past the first-link table (residue <= 32)."""
+    g = _mixed_bc(seed, shape)
+    flat = g.flags.reshape(-1)
+    fluid = np.flatnonzero(flat == G.FLUID)
+    drop = (len(fluid) - residue) % 128
+    flat[fluid[len(fluid) - drop:]] = G.WALL
+    assert int(np.count_nonzero(flat == G.FLUID)) % 128 == residue
+    return g
+
+
+@pytest.mark.parametrize("residue", [1, 17, 32, 33, 64, 65])
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16])
+def test_even_links_with_ragged_last_tiles(residue, storage):
+    # the even step's link maps, applied inside the plain, paired and
+    # bulk-staged kernels, give the same bits whatever the remainder of N_F
+    g = _mixed_bc_residue(residue)
+    kw = dict(q=27, op=P.TRT, force=(1e-5, 2e-6, 0.0), storage=storage, scale_exp=20)
+    with gpu_domain(g, **kw) as ref:
+        ref.set_launch(0, 128, 1)
+        ref.step(5)
+        want, _ = ref.get_state()
+    for shape in ((64, 1, 0), (64, 2, 1), (64, 4, 1), (128, 2, 1), (64, 2, 2), (64, 2, 3), (64, 4, 3),
+                  (128, 4, 3)):
+        with gpu_domain(g, **kw) as d:
+            d.set_launch(0, *shape)
+            d.step(5)
+            got, _ = d.get_state()
+            assert d.device_error() == 0
+        assert np.array_equal(got, want), shape
+
+
 @pytest.mark.parametrize("stages", [2, 3, 4])
 @pytest.mark.parametrize("case", ["sweep96_lex", "sweep96_brick", "dense96", "bed_links", "bf16"])
 def test_window_staged_odd_step_over_many_tiles(case, stages):
