@@ -313,13 +313,28 @@ slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher);
  *            link.  The codes ((Q-1) x S x 2 bytes) are built and allocated
  *            on the first selection of this variant (SLBM_ENOMEM if the
  *            allocation fails);
- * variant 5: odd step only, as variant 2 with 1 cell per thread, the kernel
- *            held to 64 registers a thread (more resident warps, some
- *            registers spilled to L1).
+ * variant 5: SRT/TRT: odd step only, as variant 2 with 1 cell per thread,
+ *            the kernel held to 64 registers a thread (more resident warps,
+ *            some registers spilled to L1).  MRT, central-moment and
+ *            cumulant domains: both steps, 128 x 1 (odd with the L2 index
+ *            prefetch), the kernels held to five resident blocks a
+ *            multiprocessor (at most 102 registers a thread);
+ * variant 6: odd step only, sparse SRT/TRT: 128 threads (one tile of cells)
+ *            and `cells` (2..4) shared-memory stages: a producer warp copies
+ *            each tile's 16-bit window codes, own rows and gather windows in
+ *            with the bulk-copy engine while four warps compute the previous
+ *            tile from shared memory.  The window table and codes
+ *            ((S / 128) x (Q-1) x 16 + (Q-1) x S x 2 bytes) are built on the
+ *            first selection (SLBM_ENOMEM if the allocation fails).
+ * Operators: MRT, central-moment and cumulant domains run even variants 0
+ * and 5 (MRT also 2) with 1 or 2 cells per thread and odd variants 0, 2, 3
+ * (no links) and 5; the rest SLBM_EUNSUPPORTED.  The hybrid cell order runs
+ * one odd shape: 128 x 1, variant 2 (the full bricks by their own kernel).
  * Defaults: even variant 2, 64 x 4 (FP16 D3Q27: variant 3, tile 128, 4
  * stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and BF16: variant 0,
- * 64 x 2); odd variant 2, 128 x 1.  Results are bit-for-bit the same for
- * every shape. */
+ * 64 x 2; central-moment and cumulant: variant 5, 128 x 1); odd variant 2,
+ * 128 x 1 (MRT, central-moment and cumulant: variant 5, 128 x 1).  Results
+ * are bit-for-bit the same for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch

@@ -233,12 +233,12 @@ __device__ __forceinline__ void aa_even_cells(typename Store<ST>::T *__restrict_
     }
 }
 
-// BC: the domain has inlet/outlet links; the kernel applies their maps to
-// the link slots it stored (EvenLinks; dynamic shared memory: 3 x blockDim x
-// CPT floats).
-template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false, bool BC = false>
-__global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
-                                                      int32_t nf, CollideParams p, EvenLinks lk = {}) {
+// The even step of a block's cells.  BC: the domain has inlet/outlet links;
+// the kernel applies their maps to the link slots it stored (EvenLinks;
+// dynamic shared memory: 3 x blockDim x CPT floats).
+template <int Q, int ST, int CPT, int OP, bool PACK, bool BC>
+__device__ __forceinline__ void aa_even_body(typename Store<ST>::T *__restrict__ pdf, int32_t S, int32_t nf,
+                                             const CollideParams &p, const EvenLinks &lk) {
     const int32_t k0 = (blockIdx.x * blockDim.x + threadIdx.x) * CPT;
     if constexpr (BC) {
         extern __shared__ float even_us[];
@@ -263,6 +263,12 @@ __global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__r
         Vel u[CPT];
         aa_even_cells<Q, ST, CPT, OP, PACK>(pdf, S, nf, p, k0, u);
     }
+}
+
+template <int Q, int ST, int CPT, int OP = OP_TRT, bool PACK = false, bool BC = false>
+__global__ void __launch_bounds__(256) aa_even_kernel(typename Store<ST>::T *__restrict__ pdf, int32_t S,
+                                                      int32_t nf, CollideParams p, EvenLinks lk = {}) {
+    aa_even_body<Q, ST, CPT, OP, PACK, BC>(pdf, S, nf, p, lk);
 }
 
 __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
@@ -433,6 +439,26 @@ __global__ void __launch_bounds__(256, 4) aa_odd_kernel_r64(typename Store<ST>::
                                                             CollideParams p, int32_t *err, int32_t pf_dist) {
     aa_odd_body<Q, ST, 1, HAS_BC, false, false, false, OP_TRT>(pdf, P, S, nf, maps, n_links, p, err, pf_dist,
                                                                 nullptr, nullptr);
+}
+
+// The MRT, central-moment and cumulant collisions hold a cell's moments
+// through several hundred instructions; these forms of the plain kernels
+// (128 threads, 1 cell each; odd: L2 index prefetch) are held to five
+// resident blocks a multiprocessor (at most 102 registers a thread) so that
+// more warps keep memory requests in flight.
+template <int Q, int ST, int OP, bool BC>
+__global__ void __launch_bounds__(128, 5) aa_even_kernel_b5(typename Store<ST>::T *__restrict__ pdf, int32_t S,
+                                                            int32_t nf, CollideParams p, EvenLinks lk) {
+    aa_even_body<Q, ST, 1, OP, false, BC>(pdf, S, nf, p, lk);
+}
+
+template <int Q, int ST, int OP, bool HAS_BC>
+__global__ void __launch_bounds__(128, 5) aa_odd_kernel_b5(typename Store<ST>::T *__restrict__ pdf,
+                                                           const int32_t *__restrict__ P, int32_t S, int32_t nf,
+                                                           const LinkMap *__restrict__ maps, int32_t n_links,
+                                                           CollideParams p, int32_t *err, int32_t pf_dist) {
+    aa_odd_body<Q, ST, 1, HAS_BC, false, false, false, OP>(pdf, P, S, nf, maps, n_links, p, err, pf_dist, nullptr,
+                                                           nullptr);
 }
 
 

@@ -156,8 +156,10 @@ static cudaError_t launch_even_plain(const Domain &d, int threads, cudaStream_t 
 
 // MRT (D3Q19), central-moment and cumulant (D3Q27) domains: the plain even
 // kernel (1 or 2 cells per thread; MRT variant 2: the 2 cells collided in
-// pairs) and the odd kernel (1 or 2 cells, L2 index prefetch unless variant 0;
-// checked mode), with the operator's collision.
+// pairs; variant 5: 128 x 1 held to five resident blocks) and the odd kernel
+// (1 or 2 cells, L2 index prefetch unless variant 0; variant 3: slots re-read
+// before the scatter, no links; variant 5: 128 x 1 held to five resident
+// blocks; checked mode), with the operator's collision.
 template <int Q, int ST, int OP>
 static cudaError_t launch_moment_op(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
@@ -167,6 +169,15 @@ static cudaError_t launch_moment_op(const Domain &d, int parity, cudaStream_t st
     const CollideParams p = d.collide_params();
     auto grid = [&](int cells) { return dim3((unsigned)((nf + sh.threads * cells - 1) / (sh.threads * cells))); };
     if (parity == 0) {
+        if (sh.variant == 5) {                 // register-bounded, 128 x 1
+            const dim3 g5((unsigned)((nf + 127) / 128));
+            if (d.n_bcells > 0)
+                aa_even_kernel_b5<Q, ST, OP, true><<<g5, 128, 3 * 128 * sizeof(float), st>>>(pdf, S, nf, p,
+                                                                                            even_links_of(d));
+            else
+                aa_even_kernel_b5<Q, ST, OP, false><<<g5, 128, 0, st>>>(pdf, S, nf, p, EvenLinks{});
+            return cudaGetLastError();
+        }
         if (sh.cells == 1) return launch_even_plain<Q, ST, 1, OP>(d, sh.threads, st);
         if constexpr (OP == OP_MRT) {
             if (sh.variant == 2) return launch_even_plain<Q, ST, 2, OP, true>(d, sh.threads, st);
@@ -182,6 +193,18 @@ static cudaError_t launch_moment_op(const Domain &d, int parity, cudaStream_t st
         auto kc = bc ? aa_odd_kernel<Q, ST, 1, true, true, false, false, OP>
                      : aa_odd_kernel<Q, ST, 1, false, true, false, false, OP>;
         kc<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, 0, nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    if (sh.variant == 5) {                     // register-bounded, 128 x 1, L2 index prefetch
+        auto kb = bc ? aa_odd_kernel_b5<Q, ST, OP, true> : aa_odd_kernel_b5<Q, ST, OP, false>;
+        const int32_t pfb = (int32_t)persistent_grid(kb, 128, INT32_MAX);
+        kb<<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfb);
+        return cudaGetLastError();
+    }
+    if (sh.variant == 3 && !bc) {              // slots re-read before the scatter, L2 index prefetch
+        auto kr = aa_odd_kernel<Q, ST, 1, false, false, true, false, OP>;
+        const int32_t pfr = (int32_t)persistent_grid(kr, sh.threads, INT32_MAX);
+        kr<<<grid(1), sh.threads, 0, st>>>(pdf, P, S, nf, maps, nl, p, err, pfr, nullptr, nullptr);
         return cudaGetLastError();
     }
     const int cells = sh.cells == 2 ? 2 : 1;

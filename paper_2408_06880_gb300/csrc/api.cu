@@ -95,19 +95,24 @@ CollideParams Domain::collide_params() const {
     return p;
 }
 
-// Default launch shapes of a domain's storage.  Even step: cells collided in
-// pairs (measured faster except for FP16 MRT and untimed BF16); FP16 D3Q27
-// from bulk-staged tiles.  Odd step: 128 x 1 with the L2 index prefetch.
+// Default launch shapes of a domain's operator and storage.  Even step: cells
+// collided in pairs (measured faster except for FP16 MRT and untimed BF16);
+// FP16 D3Q27 from bulk-staged tiles; the central-moment and cumulant
+// collisions 128 x 1, register-bounded.  Odd step: 128 x 1 with the L2
+// index prefetch, register-bounded for the moment-space operators (all
+// measured fastest on the 256^3 porosity-0.5 domain).
 static void default_shapes(Domain &d) {
     d.shape[0] = LaunchShape{64, 2, 0};
     d.shape[1] = LaunchShape{128, 1, 2};
-    if (d.layout == SLBM_LAYOUT_SPARSE && d.storage != SLBM_BF16) {
-        if (d.op == SLBM_CM || d.op == SLBM_CUMULANT)
-            d.shape[0] = LaunchShape{128, 1, 0};
-        else if (d.op != SLBM_MRT)
-            d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
-        else if (d.storage == SLBM_FP32)
-            d.shape[0] = LaunchShape{64, 2, 2};
+    if (d.layout != SLBM_LAYOUT_SPARSE) return;
+    if (d.op == SLBM_CM || d.op == SLBM_CUMULANT) {              // register-bounded, both steps
+        d.shape[0] = LaunchShape{128, 1, 5};
+        d.shape[1] = LaunchShape{128, 1, 5};
+    } else if (d.op == SLBM_MRT) {                                // paired even step in FP32
+        if (d.storage == SLBM_FP32) d.shape[0] = LaunchShape{64, 2, 2};
+        d.shape[1] = LaunchShape{128, 1, 5};
+    } else if (d.storage != SLBM_BF16) {
+        d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
     }
 }
 
@@ -654,14 +659,26 @@ slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher) {
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant) {
     if (!h || (parity != 0 && parity != 1)) return err(SLBM_EINVAL, "bad handle or parity");
     if (h->d.pull()) return err(SLBM_EUNSUPPORTED, "the pull layout has one launch shape");
-    if (h->d.op == SLBM_MRT && variant != 0 && variant != 2)
-        return err(SLBM_EUNSUPPORTED, "MRT domains run launch variants 0 and 2");
-    if ((h->d.op == SLBM_CM || h->d.op == SLBM_CUMULANT) && !(variant == 0 || (parity == 1 && variant == 2)))
-        return err(SLBM_EUNSUPPORTED, "central-moment and cumulant domains run variant 0 (and 2 for the odd step)");
-    if ((h->d.op == SLBM_CM || h->d.op == SLBM_CUMULANT) && parity == 0 && cells == 4)
-        return err(SLBM_EUNSUPPORTED, "central-moment and cumulant even step: 1 or 2 cells per thread");
-    if (h->d.op == SLBM_MRT && parity == 0 && cells == 4)
-        return err(SLBM_EUNSUPPORTED, "MRT even step: 1 or 2 cells per thread");
+    const bool moment = h->d.op == SLBM_MRT || h->d.op == SLBM_CM || h->d.op == SLBM_CUMULANT;
+    if (moment) {
+        // even: 0, 2 (MRT pairs), 5; odd: 0, 2, 3 (no links), 5 -- 5 is 128 x 1 only
+        const bool okv = parity == 0 ? (variant == 0 || variant == 5 || (h->d.op == SLBM_MRT && variant == 2))
+                                     : (variant == 0 || variant == 2 || variant == 3 || variant == 5);
+        if (!okv)
+            return err(SLBM_EUNSUPPORTED, "MRT, central-moment and cumulant domains run even variants 0 and 5 "
+                                          "(MRT also 2) and odd variants 0, 2, 3 and 5");
+        if (parity == 0 && cells == 4)
+            return err(SLBM_EUNSUPPORTED, "MRT, central-moment and cumulant even step: 1 or 2 cells per thread");
+        if (parity == 1 && variant == 3 && h->d.n_links > 0)
+            return err(SLBM_EUNSUPPORTED, "odd variant 3 (slots re-read) covers domains without inlet/outlet links");
+        if (variant == 5) {
+            if (threads != 128 || cells != 1)
+                return err(SLBM_EINVAL, "variant 5 of the moment-space operators: 128 threads, 1 cell each");
+            h->d.shape[parity] = LaunchShape{threads, cells, variant};
+            drop_graphs(h->d);
+            return ok();
+        }
+    }
     if (parity == 1 && h->d.order == SLBM_ORDER_HYBRID && h->d.layout == SLBM_LAYOUT_SPARSE &&
         !(threads == 128 && cells == 1 && variant == 2))
         return err(SLBM_EUNSUPPORTED, "the hybrid cell order has one odd-step shape (full bricks + 128 x 1, variant 2)");

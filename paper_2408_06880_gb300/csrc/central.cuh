@@ -29,7 +29,8 @@
 //   post-collision second ones -- e.g. kappa_220 = rho (m_200 m_020 + 2
 //   m_110^2), kappa_222 = rho (m_200 m_020 m_002 + 2 m_200 m_011^2 + ... +
 //   8 m_110 m_101 m_011), m = kappa / rho -- written in deviations.
-// Then g* = inverse transform of (Dk* - B).
+// Then g* = inverse transform of (Dk* - B), B formed per moment where it is
+// used.
 #pragma once
 
 namespace slbm {
@@ -94,67 +95,76 @@ __device__ __forceinline__ Vel collide_central(float (&g)[27], const CollidePara
     }
 #pragma unroll
     for (int l = 0; l < 9; ++l) to_central(k[l], k[l + 9], k[l + 18], uz);
-    // B and the deviations Dk = kappa(g) + B
-    float B[27];
-#pragma unroll
-    for (int q = 0; q < 27; ++q) {
+    // B of moment q: prod(m + d) - prod(m), nested so that no O(1) terms
+    // cancel, minus drho prod(m).  Each moment takes Dk = kappa(g) + B, its
+    // relaxed value Dk*, and leaves kappa(g*) = Dk* - B, with B formed where
+    // it is used (one moment at a time: no array of B is kept).
+    auto Bq = [&](int q) {
         const int a = q % 3, b = (q / 3) % 3, c = q / 9;
         const float ma = m1(a), mb = m1(b), mc = m1(c);
         const float da = d1(a, ux), db = d1(b, uy), dc = d1(c, uz);
-        // prod(m + d) - prod(m), nested so that no O(1) terms cancel
         const float diff = da * ((mb + db) * (mc + dc)) + ma * (db * (mc + dc) + mb * dc);
-        B[q] = diff - drho * (ma * mb * mc);
-        k[q] += B[q];
-    }
+        return diff - drho * (ma * mb * mc);
+    };
     constexpr int XX = 2, YY = 6, ZZ = 18, XY = 4, XZ = 10, YZ = 12;
     const float w = p.omega_p, wb = p.mrt[0], wh = p.mrt[1];
     // orders 0 and 1
-    k[0] = 0.0f;
-    k[1] = 0.5f * p.fx;
-    k[3] = 0.5f * p.fy;
-    k[9] = 0.5f * p.fz;
-    // order 2
+    k[0] = 0.0f - Bq(0);
+    k[1] = 0.5f * p.fx - Bq(1);
+    k[3] = 0.5f * p.fy - Bq(3);
+    k[9] = 0.5f * p.fz - Bq(9);
+    // order 2: trace * (1 - bulk), normal differences and off-diagonals * (1 - omega+)
+    const float Bxx = Bq(XX), Byy = Bq(YY), Bzz = Bq(ZZ), Bxy = Bq(XY), Bxz = Bq(XZ), Byz = Bq(YZ);
+    float sxx, syy, szz, sxy, sxz, syz;              // relaxed deviations Dk*
     {
-        const float T = (k[XX] + k[YY] + k[ZZ]) * (1.0f - wb);
-        const float D1 = (k[XX] - k[YY]) * (1.0f - w), D2 = (k[XX] - k[ZZ]) * (1.0f - w);
-        k[XX] = (T + D1 + D2) * (1.0f / 3.0f);
-        k[YY] = (T - 2.0f * D1 + D2) * (1.0f / 3.0f);
-        k[ZZ] = (T + D1 - 2.0f * D2) * (1.0f / 3.0f);
-        k[XY] *= 1.0f - w;
-        k[XZ] *= 1.0f - w;
-        k[YZ] *= 1.0f - w;
+        const float dxx = k[XX] + Bxx, dyy = k[YY] + Byy, dzz = k[ZZ] + Bzz;
+        const float T = (dxx + dyy + dzz) * (1.0f - wb);
+        const float D1 = (dxx - dyy) * (1.0f - w), D2 = (dxx - dzz) * (1.0f - w);
+        sxx = (T + D1 + D2) * (1.0f / 3.0f);
+        syy = (T - 2.0f * D1 + D2) * (1.0f / 3.0f);
+        szz = (T + D1 - 2.0f * D2) * (1.0f / 3.0f);
+        sxy = (k[XY] + Bxy) * (1.0f - w);
+        sxz = (k[XZ] + Bxz) * (1.0f - w);
+        syz = (k[YZ] + Byz) * (1.0f - w);
     }
+    k[XX] = sxx - Bxx;
+    k[YY] = syy - Byy;
+    k[ZZ] = szz - Bzz;
+    k[XY] = sxy - Bxy;
+    k[XZ] = sxz - Bxz;
+    k[YZ] = syz - Byz;
     if constexpr (OP == OP_CM) {
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             const int o = q % 3 + (q / 3) % 3 + q / 9;
-            if (o >= 3) k[q] *= 1.0f - wh;
+            if (o >= 3) {
+                const float B = Bq(q);
+                k[q] = (k[q] + B) * (1.0f - wh) - B;
+            }
         }
     } else {
         // normalised post-collision second moments as deviations: m_aa = 1/3 + a_a
-        const float ax = k[XX] * ir, ay = k[YY] * ir, az = k[ZZ] * ir;
-        const float bxy = k[XY] * ir, bxz = k[XZ] * ir, byz = k[YZ] * ir;
+        const float ax = sxx * ir, ay = syy * ir, az = szz * ir;
+        const float bxy = sxy * ir, bxz = sxz * ir, byz = syz * ir;
         constexpr float t3 = 1.0f / 3.0f;
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             const int o = q % 3 + (q / 3) % 3 + q / 9;
-            if (o == 3 || o == 5) k[q] = 0.0f;
+            if (o == 3 || o == 5) k[q] = 0.0f - Bq(q);
         }
         // order 4: (2,2,0)-type and (2,1,1)-type, each minus its equilibrium
-        k[2 + 6] = rho * ((ax + ay) * t3 + ax * ay + 2.0f * bxy * bxy);          // 220
-        k[2 + 18] = rho * ((ax + az) * t3 + ax * az + 2.0f * bxz * bxz);         // 202
-        k[6 + 18] = rho * ((ay + az) * t3 + ay * az + 2.0f * byz * byz);         // 022
-        k[2 + 3 + 9] = rho * ((t3 + ax) * byz + 2.0f * bxy * bxz);               // 211
-        k[1 + 6 + 9] = rho * ((t3 + ay) * bxz + 2.0f * bxy * byz);               // 121
-        k[1 + 3 + 18] = rho * ((t3 + az) * bxy + 2.0f * bxz * byz);              // 112
+        k[2 + 6] = rho * ((ax + ay) * t3 + ax * ay + 2.0f * bxy * bxy) - Bq(2 + 6);          // 220
+        k[2 + 18] = rho * ((ax + az) * t3 + ax * az + 2.0f * bxz * bxz) - Bq(2 + 18);        // 202
+        k[6 + 18] = rho * ((ay + az) * t3 + ay * az + 2.0f * byz * byz) - Bq(6 + 18);        // 022
+        k[2 + 3 + 9] = rho * ((t3 + ax) * byz + 2.0f * bxy * bxz) - Bq(2 + 3 + 9);           // 211
+        k[1 + 6 + 9] = rho * ((t3 + ay) * bxz + 2.0f * bxy * byz) - Bq(1 + 6 + 9);           // 121
+        k[1 + 3 + 18] = rho * ((t3 + az) * bxy + 2.0f * bxz * byz) - Bq(1 + 3 + 18);         // 112
         // order 6: 222 minus 1/27
         k[26] = rho * ((ax + ay + az) * (t3 * t3) + (ax * ay + ax * az + ay * az) * t3 + ax * ay * az +
                        2.0f * ((t3 + ax) * byz * byz + (t3 + ay) * bxz * bxz + (t3 + az) * bxy * bxy) +
-                       8.0f * bxy * bxz * byz);
+                       8.0f * bxy * bxz * byz) - Bq(26);
     }
-    // back: kappa(g*) = Dk* - B, inverse passes z, y, x
-#pragma unroll
-    for (int q = 0; q < 27; ++q) k[q] -= B[q];
+    // back: inverse passes z, y, x
 #pragma unroll
     for (int l = 0; l < 9; ++l) from_central(k[l], k[l + 9], k[l + 18], uz);
 #pragma unroll

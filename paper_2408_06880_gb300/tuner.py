@@ -21,7 +21,8 @@ import numpy as np
 from . import _capi as A
 
 EVEN_SHAPES = [(64, 1, 0), (64, 2, 0), (128, 2, 0), (64, 4, 0), (128, 2, 1), (128, 4, 1), (64, 2, 1),
-               (64, 2, 2), (128, 2, 2), (64, 4, 2), (128, 2, 3), (128, 4, 3), (64, 2, 3)]
+               (64, 2, 2), (128, 2, 2), (64, 4, 2), (128, 2, 3), (128, 4, 3), (64, 2, 3), (128, 1, 0),
+               (128, 1, 5)]
 ODD_SHAPES = [(128, 1, 2), (64, 1, 2), (256, 1, 2), (128, 1, 3), (256, 1, 3), (128, 1, 4), (64, 1, 4), (128, 1, 0),
               (128, 2, 1), (256, 1, 5), (128, 1, 5)]
 POOL_SHAPES = [(64, 0), (64, 8), (128, 4), (96, 4)]
@@ -63,17 +64,20 @@ def size_class(n_fluid: int) -> int:
 
 def _valid(info: dict, parity: int, shape) -> bool:
     """Shapes the library accepts for this domain: no bulk-staged BF16 (even
-    variants 1 and 3, odd variant 1); MRT runs variants 0 and 2 with at most
-    2 cells per thread; the central-moment and cumulant operators variant 0
-    (and 2 for the odd step) with at most 2."""
+    variants 1 and 3, odd variant 1); the moment-space operators (MRT,
+    central moments, cumulants) run even variants 0 and 5 (MRT also 2) and odd
+    variants 0, 2, 3 (without links) and 5, at most 2 cells per thread,
+    variant 5 as 128 x 1; even variant 5 exists for them only."""
     staged = shape[2] == 1 or (parity == 0 and shape[2] == 3)
     if staged and info["storage"] == A.BF16:
         return False
-    if info["op"] == A.MRT:
-        return shape[2] in (0, 2) and shape[1] <= 2
-    if info["op"] in (A.CM, A.CUMULANT):
-        return shape[1] <= 2 and (shape[2] == 0 or (parity == 1 and shape[2] == 2))
-    return True
+    if info["op"] in (A.MRT, A.CM, A.CUMULANT):
+        if shape[2] == 5:
+            return tuple(shape[:2]) == (128, 1)
+        if parity == 0:
+            return shape[1] <= 2 and (shape[2] == 0 or (info["op"] == A.MRT and shape[2] == 2))
+        return shape[1] <= 2 and (shape[2] in (0, 2) or (shape[2] == 3 and info.get("n_bc_links", 0) == 0))
+    return shape[2] != 5 or parity == 1
 
 
 def _time_parity(dom, parity: int, shape, reps: int, stream) -> float:

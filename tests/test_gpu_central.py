@@ -95,7 +95,8 @@ def test_central_shapes_and_pull_layout_are_bitwise_identical(gop, storage):
         want = ref.macroscopic(P.ORDER_CELLS)
         state, _ = ref.get_state()
     for even, odd in (((128, 1, 0), (128, 1, 0)), ((64, 2, 0), (256, 2, 2)), ((256, 1, 0), (64, 1, 2)),
-                      ((32, 2, 0), (128, 2, 0))):
+                      ((32, 2, 0), (128, 2, 0)), ((128, 1, 5), (128, 1, 5)), ((64, 1, 0), (128, 1, 3)),
+                      ((128, 1, 5), (256, 1, 3))):
         with gpu_domain(g, **kw) as d:
             d.set_launch(0, *even)
             d.set_launch(1, *odd)
@@ -105,6 +106,27 @@ def test_central_shapes_and_pull_layout_are_bitwise_identical(gop, storage):
         d.step(7)
         got = d.macroscopic(P.ORDER_CELLS)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+@pytest.mark.parametrize("gop", [P.CM, P.CUMULANT], ids=["cm", "cumulant"])
+def test_central_register_bounded_kernels_with_links(gop):
+    # variant 5 (128 x 1, at most 102 registers) of both steps, with the
+    # even step's link maps and the odd step's, gives the plain kernels' bits
+    g = _mixed_bc(16, (24, 19, 17))
+    kw = dict(q=27, op=gop, force=(0.0, 0.0, 0.0))
+    with gpu_domain(g, **kw) as ref:
+        ref.set_launch(0, 128, 1)
+        ref.set_launch(1, 128, 1)
+        ref.step(9)
+        want = ref.get_state()[0]
+    with gpu_domain(g, **kw) as d:
+        d.set_launch(0, 128, 1, 5)
+        d.set_launch(1, 128, 1, 5)
+        d.step(9)
+        assert np.array_equal(d.get_state()[0], want)
+        assert d.device_error() == 0
+        with pytest.raises(P.SlbmError):
+            d.set_launch(1, 128, 1, 3)            # slots re-read: domains without links only
 
 
 def test_central_checked_mode_matches_unchecked():
@@ -128,7 +150,8 @@ def test_central_refusals():
             gpu_domain(g, q=27, op=op, layout=P.DENSE)
     with gpu_domain(g, q=27, op=P.CM) as d:
         for parity, shape in ((0, (128, 2, 2)), (0, (128, 2, 3)), (0, (64, 4, 0)), (1, (128, 2, 1)),
-                              (1, (128, 1, 3)), (1, (128, 1, 6))):
+                              (1, (128, 1, 4)), (1, (128, 1, 6)), (0, (64, 1, 5)), (1, (128, 2, 5)),
+                              (0, (128, 1, 1))):
             with pytest.raises(P.SlbmError):
                 d.set_launch(parity, *shape)
         for bulk, high in ((0.0, 1.0), (1.0, 2.5), (float("nan"), 1.0)):

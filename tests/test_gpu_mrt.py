@@ -79,7 +79,8 @@ def test_mrt_shapes_and_pull_layout_are_bitwise_identical(storage):
         want = ref.macroscopic(P.ORDER_CELLS)
         state, _ = ref.get_state()
     for even, odd in (((128, 1, 0), (128, 1, 0)), ((64, 2, 0), (256, 2, 2)), ((256, 1, 0), (64, 1, 2)),
-                      ((64, 2, 2), (128, 1, 2)), ((256, 2, 2), (128, 2, 0))):
+                      ((64, 2, 2), (128, 1, 2)), ((256, 2, 2), (128, 2, 0)), ((128, 1, 5), (128, 1, 5)),
+                      ((64, 2, 2), (128, 1, 3))):
         with gpu_domain(g, **kw) as d:
             d.set_launch(0, *even)
             d.set_launch(1, *odd)

@@ -1,7 +1,8 @@
 """Host logic of the launch-shape autotuner on CPU: every candidate shape lies
 in the ranges the C ABI documents for its parity and variant, the per-domain
-filter drops exactly the shapes a domain refuses (bulk-staged BF16; MRT
-beyond variants 0/2 and 2 cells), and the JSON cache round-trips."""
+filter drops exactly the shapes a domain refuses (bulk-staged BF16; the
+moment-space operators beyond their variants and 2 cells; the even variant 5
+of the moment-space operators for SRT/TRT), and the JSON cache round-trips."""
 import pytest
 
 from paper_2408_06880_gb300 import _capi as A
@@ -18,6 +19,8 @@ def _documented(parity, shape):
             return threads in (64, 128) and cells in (2, 4)
         if variant == 2:
             return warp_multiple and cells in (2, 4)
+        if variant == 5:
+            return threads == 128 and cells == 1
         return False
     if variant == 0:
         return warp_multiple and cells in (1, 2)
@@ -39,14 +42,15 @@ def test_every_candidate_is_a_documented_shape():
     assert len(set(T.ODD_SHAPES)) == len(T.ODD_SHAPES)
 
 
-def _info(op=A.TRT, storage=A.FP32):
-    return {"op": op, "storage": storage}
+def _info(op=A.TRT, storage=A.FP32, links=0):
+    return {"op": op, "storage": storage, "n_bc_links": links}
 
 
 @pytest.mark.parametrize("storage", [A.FP32, A.FP16])
 def test_srt_trt_domains_take_every_candidate(storage):
     for op in (A.SRT, A.TRT):
-        assert all(T._valid(_info(op, storage), 0, s) for s in T.EVEN_SHAPES)
+        # even variant 5 is the moment-space operators' register-bounded kernel
+        assert all(T._valid(_info(op, storage), 0, s) == (s[2] != 5) for s in T.EVEN_SHAPES)
         assert all(T._valid(_info(op, storage), 1, s) for s in T.ODD_SHAPES)
 
 
@@ -54,17 +58,25 @@ def test_bf16_drops_only_the_bulk_staged_shapes():
     info = _info(A.TRT, A.BF16)
     dropped_even = [s for s in T.EVEN_SHAPES if not T._valid(info, 0, s)]
     dropped_odd = [s for s in T.ODD_SHAPES if not T._valid(info, 1, s)]
-    assert dropped_even and all(s[2] in (1, 3) for s in dropped_even)
+    assert dropped_even and all(s[2] in (1, 3, 5) for s in dropped_even)
     assert all(s[2] == 1 for s in dropped_odd)
     # odd variant 3 (slots re-read) is not staged: BF16 keeps it
     assert T._valid(info, 1, (128, 1, 3))
 
 
-def test_mrt_keeps_variants_0_and_2_with_at_most_two_cells():
-    info = _info(A.MRT, A.FP32)
+@pytest.mark.parametrize("op", [A.MRT, A.CM, A.CUMULANT])
+@pytest.mark.parametrize("links", [0, 5])
+def test_moment_operators_keep_their_variants(op, links):
+    info = _info(op, A.FP32, links)
     for parity, shapes in ((0, T.EVEN_SHAPES), (1, T.ODD_SHAPES)):
         for s in shapes:
-            assert T._valid(info, parity, s) == (s[2] in (0, 2) and s[1] <= 2), (parity, s)
+            if s[2] == 5:
+                want = tuple(s[:2]) == (128, 1)
+            elif parity == 0:
+                want = s[1] <= 2 and (s[2] == 0 or (op == A.MRT and s[2] == 2))
+            else:
+                want = s[1] <= 2 and (s[2] in (0, 2) or (s[2] == 3 and links == 0))
+            assert T._valid(info, parity, s) == want, (parity, s)
 
 
 def test_size_class_is_the_log2_bucket():
