@@ -66,8 +66,13 @@ def parse():
     ap.add_argument("--shape-odd", default=None, help="threads,cells,variant of the odd kernel")
     ap.add_argument("--cell-order", choices=["lex", "brick8"], default="lex",
                     help="compacted cell order of the timed domains")
-    ap.add_argument("--mode", default="kernel", choices=["kernel", "serve", "workloads"],
-                    help="kernel: the porosity sweep (default); serve: the permeability-request stream")
+    ap.add_argument("--mode", default="kernel", choices=["kernel", "serve", "workloads", "case"],
+                    help="kernel: the porosity sweep (default); serve: the permeability-request stream; "
+                         "workloads: the application-shaped domains; case: one domain stepped --lbm-steps "
+                         "times without timing (the small cases the profiles are captured on)")
+    ap.add_argument("--case", default="bed", choices=["bed", "bed16", "cm", "cumulant"],
+                    help="case mode: the particle bed (FP32 / FP16, D3Q27 TRT, tuned shapes) or a "
+                         "--size^3 porosity-0.5 packing with the central-moment / cumulant operator")
     ap.add_argument("--requests", type=int, default=64, help="serve mode: number of requests")
     ap.add_argument("--max-steps", type=int, default=20000, help="serve mode: step cap per request")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="serve mode: HBM admission budget")
@@ -803,6 +808,7 @@ def run_workloads(a, pairs=10):
                      trt_magic=MAGIC, storage=storage, scale_exp=P.auto_scale_exp(0.06) if storage else 0,
                      layout=layout, stream=stream, cell_order=order)
         shapes = None
+        mem = d.memory_bytes()              # before the tuner builds its candidates' optional tables
         if layout == P.SPARSE and order != P.ORDER_HYBRID:
             from paper_2408_06880_gb300 import tuner
             shapes = tuner.tune_domain(d, reps=5, use_cache=False, stream=stream)   # state restored
@@ -823,7 +829,7 @@ def run_workloads(a, pairs=10):
              "layout": {P.SPARSE: "sparse", P.DENSE: "dense"}[layout], "n_voxels": int(g.flags.size),
              "n_fluid": nf, "fluid_fraction": round(nf / g.flags.size, 5),
              "mflups": round(nf / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
-             "bytes_per_fluid_cell": round(d.memory_bytes() / nf, 2)}
+             "bytes_per_fluid_cell": round(mem / nf, 2)}
         if shapes:
             r["shapes"] = {"even": list(shapes["even"]), "odd": list(shapes["odd"]), "by": "autotuner"}
         if per is not None:
@@ -845,8 +851,39 @@ def run_workloads(a, pairs=10):
     return out
 
 
+def run_case(a):
+    """One domain stepped `--lbm-steps` times with its default launch shapes
+    (the particle bed: the shapes the autotuner picks for it), no timing: the
+    small cases the ncu summaries under profiles/ are captured on."""
+    import torch
+    import geometry as G
+    import paper_2408_06880_gb300 as P
+    stream = torch.cuda.Stream()
+    if a.case in ("bed", "bed16"):
+        g = G.particle_bed()
+        storage = P.FP32 if a.case == "bed" else P.FP16
+        d = P.Domain(g.flags, periodic=g.periodic, inlet_u=g.inlet_u, rho_out=g.rho_out, q=27, op=P.TRT,
+                     omega=OMEGA, trt_magic=MAGIC, storage=storage,
+                     scale_exp=P.auto_scale_exp(0.06) if storage else 0, stream=stream)
+        even, odd = ((64, 4, 2), (64, 1, 2)) if a.case == "bed" else ((128, 2, 1), (128, 1, 2))
+        d.set_launch(0, *even)
+        d.set_launch(1, *odd)
+    else:
+        g = geometry_for(0.5, a.size)
+        d = P.Domain(g.flags, periodic=7, q=27, op=P.CM if a.case == "cm" else P.CUMULANT, omega=OMEGA,
+                     force=FORCE, stream=stream)
+    d.step(a.lbm_steps)
+    torch.cuda.synchronize()
+    out = {"mode": "case", "case": a.case, "n_fluid": d.n_fluid, "lbm_steps": a.lbm_steps}
+    d.close()
+    return out
+
+
 def main():
     a = parse()
+    if a.mode == "case" and a.impl == "ours":
+        print(json.dumps(run_case(a)), flush=True)
+        return
     if a.mode == "workloads" and a.impl == "ours":
         print(json.dumps(run_workloads(a)), flush=True)
         return

@@ -15,7 +15,7 @@
 // (1, 0, 1/3) about 0, so kappa(f) = kappa(g) + prod (m + d) with the
 // shifts d = (0, -u, u^2), and Dk = kappa(g) + B with
 // B = [prod (m + d) - prod m] - (rho - 1) prod m evaluated without
-// subtracting nearly equal numbers.  Relaxation (rates: omega+ on the shear
+// subtracting nearly equal numbers (see Bq below).  Relaxation (rates: omega+ on the shear
 // moments, the bulk rate on the trace of the second ones, the higher rate on
 // orders 3..6):
 //   order 0: Dk = 0;   order 1: the first central moments become +F/2 (the
@@ -66,10 +66,6 @@ __device__ __forceinline__ void from_central(float &k0, float &k1, float &k2, fl
     k2 = pl;
 }
 
-// One-dimensional factors: equilibrium moment m(a) and its shift d(a) by v.
-__device__ __forceinline__ constexpr float m1(int a) { return a == 0 ? 1.0f : (a == 1 ? 0.0f : 1.0f / 3.0f); }
-__device__ __forceinline__ float d1(int a, float v) { return a == 0 ? 0.0f : (a == 1 ? -v : v * v); }
-
 template <bool SCALED, int OP>
 __device__ __forceinline__ Vel collide_central(float (&g)[27], const CollideParams &p) {
     static_assert(OP == OP_CM || OP == OP_CUM, "central-moment operators");
@@ -95,16 +91,39 @@ __device__ __forceinline__ Vel collide_central(float (&g)[27], const CollidePara
     }
 #pragma unroll
     for (int l = 0; l < 9; ++l) to_central(k[l], k[l + 9], k[l + 18], uz);
-    // B of moment q: prod(m + d) - prod(m), nested so that no O(1) terms
-    // cancel, minus drho prod(m).  Each moment takes Dk = kappa(g) + B, its
-    // relaxed value Dk*, and leaves kappa(g*) = Dk* - B, with B formed where
-    // it is used (one moment at a time: no array of B is kept).
+    // B of moment q = (a, b, c), formed where it is used (no array of B is
+    // kept).  With an index 1, prod(m) = 0 and B = prod(m + d), a product of
+    // the factors 1, -u, 1/3 + u^2.  Otherwise m + d = m (1 + delta) per axis,
+    // delta = 0 (index 0) or 3 u^2 (index 2), and B = prod(m) (S - drho) with
+    // S = prod(1 + delta) - 1 expanded axis by axis as S' = S + delta +
+    // S delta, so that no O(1) terms cancel.
+    const float ex2 = fmaf(ux, ux, 1.0f / 3.0f), ey2 = fmaf(uy, uy, 1.0f / 3.0f), ez2 = fmaf(uz, uz, 1.0f / 3.0f);
+    const float dx3 = 3.0f * (ux * ux), dy3 = 3.0f * (uy * uy), dz3 = 3.0f * (uz * uz);
     auto Bq = [&](int q) {
         const int a = q % 3, b = (q / 3) % 3, c = q / 9;
-        const float ma = m1(a), mb = m1(b), mc = m1(c);
-        const float da = d1(a, ux), db = d1(b, uy), dc = d1(c, uz);
-        const float diff = da * ((mb + db) * (mc + dc)) + ma * (db * (mc + dc) + mb * dc);
-        return diff - drho * (ma * mb * mc);
+        if (a == 1 || b == 1 || c == 1) {
+            float r = a == 1 ? -ux : ex2;
+            if (a == 0) r = 1.0f;
+            if (b == 1) r = r * -uy;
+            if (b == 2) r = r * ey2;
+            if (c == 1) r = r * -uz;
+            if (c == 2) r = r * ez2;
+            return r;
+        }
+        float S = 0.0f;
+        bool any = false;
+        if (a == 2) {
+            S = dx3;
+            any = true;
+        }
+        if (b == 2) {
+            S = any ? fmaf(S, dy3, S + dy3) : dy3;
+            any = true;
+        }
+        if (c == 2) S = any ? fmaf(S, dz3, S + dz3) : dz3;
+        const int n2 = (a == 2) + (b == 2) + (c == 2);
+        const float M = n2 == 0 ? 1.0f : n2 == 1 ? 1.0f / 3.0f : n2 == 2 ? 1.0f / 9.0f : 1.0f / 27.0f;
+        return n2 == 0 ? -drho : M * (S - drho);
     };
     constexpr int XX = 2, YY = 6, ZZ = 18, XY = 4, XZ = 10, YZ = 12;
     const float w = p.omega_p, wb = p.mrt[0], wh = p.mrt[1];
