@@ -95,12 +95,13 @@ CollideParams Domain::collide_params() const {
     return p;
 }
 
-// Default launch shapes of a domain's operator and storage.  Even step: cells
-// collided in pairs (measured faster except for FP16 MRT and untimed BF16);
-// FP16 D3Q27 from bulk-staged tiles; the central-moment and cumulant
-// collisions 128 x 1, register-bounded.  Odd step: 128 x 1 with the L2
-// index prefetch, register-bounded for the moment-space operators (all
-// measured fastest on the 256^3 porosity-0.5 domain).
+// Default launch shapes of a domain's operator, storage and links (called
+// once its lists exist).  Even step: cells collided in pairs (measured faster
+// except for FP16 MRT and untimed BF16); FP16 D3Q27 from bulk-staged tiles;
+// the central-moment and cumulant collisions 128 x 1, register-bounded.  Odd
+// step: 128 x 1 with the L2 index prefetch, register-bounded for the
+// moment-space operators; D3Q27 as below.  All measured fastest on the 256^3
+// porosity-0.5 domain and, with links, on the particle bed.
 static void default_shapes(Domain &d) {
     d.shape[0] = LaunchShape{64, 2, 0};
     d.shape[1] = LaunchShape{128, 1, 2};
@@ -112,8 +113,16 @@ static void default_shapes(Domain &d) {
         if (d.storage == SLBM_FP32) d.shape[0] = LaunchShape{64, 2, 2};
         d.shape[1] = LaunchShape{128, 1, 5};
     } else if (d.storage != SLBM_BF16) {
-        d.shape[0] = d.storage == SLBM_FP16 && d.q == 27 ? LaunchShape{128, 4, 3} : LaunchShape{64, 4, 2};
+        d.shape[0] = LaunchShape{64, 4, 2};
+        if (d.q == 27) {
+            // D3Q27: FP16 even step from bulk-staged tiles (paired without links,
+            // 2 stages with them); odd step from staged index tiles without
+            // links, 64 x 1 with the L2 prefetch with them
+            if (d.storage == SLBM_FP16) d.shape[0] = d.n_links > 0 ? LaunchShape{128, 2, 1} : LaunchShape{128, 4, 3};
+            d.shape[1] = d.n_links > 0 ? LaunchShape{64, 1, 2} : LaunchShape{128, 2, 1};
+        }
     }
+    if (d.order == SLBM_ORDER_HYBRID) d.shape[1] = LaunchShape{128, 1, 2};   // its one odd shape
 }
 
 // d'Humieres et al. (2002) rates with omega on the stress moments.
@@ -315,7 +324,6 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     }
     for (int a = 0; a < 3; ++a) d.force[a] = s.force[a];
     d.rho_out = s.rho_out;
-    default_shapes(d);
     if (alloc) {
         if (!alloc->alloc || !alloc->free) {
             delete h;
@@ -374,6 +382,7 @@ slbm_status sparse_lbm_create(const slbm_desc *desc, const slbm_allocator *alloc
     if (!rc) rc = cx.check(cudaMemsetAsync(d.err.p, 0, sizeof(int32_t), d.stream), "memset err");
     if (!rc) rc = cx.check(cudaStreamSynchronize(d.stream), "create sync");
     cx.release(flags);
+    default_shapes(d);
     if (rc) {
         const slbm_status st = cx.status == SLBM_OK ? SLBM_ECUDA : cx.status;
         const std::string m = g_msg;
