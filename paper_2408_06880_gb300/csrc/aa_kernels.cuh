@@ -284,6 +284,11 @@ __device__ __forceinline__ void latch(int32_t *err, int32_t code) {
 // RELOAD (CPT = 1, no links): the slots are re-read from the list (an L1
 // hit) before the scatter instead of being held in registers through the
 // collision, which frees registers for more resident threads.
+// The gathers go through the read-only data path (__ldg) although the kernel
+// writes the PDF-list: each slot is read by one cell only, once, and written
+// afterwards by that same cell, so no thread ever reads a slot after it was
+// written in this launch and a line held in the read-only cache can never
+// supply a stale value that is used.
 // CODE: the slots come from the 16-bit link codes and their per-tile column
 // bases (2 bytes per link instead of 4); an escape code reads the slot from
 // the int32 list.  The decoded slot equals R(i, k) exactly.
@@ -366,7 +371,7 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         const int32_t k = kb + c * blockDim.x;
-        g[c][0] = valid[c] ? St::raw(pdf[k]) : 0.f;
+        g[c][0] = valid[c] ? St::raw(__ldg(pdf + k)) : 0.f;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             int32_t ee = e[c][i];
@@ -380,7 +385,7 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
                 }
             }
             R[c][i] = r;
-            g[c][i] = valid[c] ? St::raw(pdf[r]) : 0.f;
+            g[c][i] = valid[c] ? St::raw(__ldg(pdf + r)) : 0.f;
         }
     }
     Vel u[CPT];
@@ -529,12 +534,12 @@ __device__ __forceinline__ void odd_cell(typename Store<ST>::T *__restrict__ pdf
     using St = Store<ST>;
     int32_t R[Q];
     float g[Q];
-    g[0] = St::raw(pdf[k]);
+    g[0] = St::raw(__ldg(pdf + k));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int32_t ee = e[i];
         R[i] = (HAS_BC && ee < 0) ? i * S + k : ee;
-        g[i] = St::raw(pdf[R[i]]);
+        g[i] = St::raw(__ldg(pdf + R[i]));
     }
     const Vel u = collide<Q, St::scaled>(g, p);
     pdf[k] = St::pack(g[0]);

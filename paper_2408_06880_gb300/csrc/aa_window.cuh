@@ -223,7 +223,7 @@ __device__ __forceinline__ void window_cell(typename Store<ST>::T *__restrict__ 
         } else {                                        // a fluid neighbour outside both windows
             const int32_t e = R[(int64_t)(i - 1) * S + k];
             slot[i] = e;
-            g[i] = St::raw(pdf[e]);
+            g[i] = St::raw(__ldg(pdf + e));
         }
     }
     const Vel u = collide<Q, St::scaled>(g, p);

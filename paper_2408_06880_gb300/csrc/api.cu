@@ -113,13 +113,17 @@ static void default_shapes(Domain &d) {
         if (d.storage == SLBM_FP32) d.shape[0] = LaunchShape{64, 2, 2};
         d.shape[1] = LaunchShape{128, 1, 5};
     } else if (d.storage != SLBM_BF16) {
+        const bool f16 = d.storage == SLBM_FP16, links = d.n_links > 0;
         d.shape[0] = LaunchShape{64, 4, 2};
-        if (d.q == 27) {
+        if (d.q == 19) {
+            if (f16) d.shape[1] = LaunchShape{256, 1, 2};
+        } else {
             // D3Q27: FP16 even step from bulk-staged tiles (paired without links,
-            // 2 stages with them); odd step from staged index tiles without
-            // links, 64 x 1 with the L2 prefetch with them
-            if (d.storage == SLBM_FP16) d.shape[0] = d.n_links > 0 ? LaunchShape{128, 2, 1} : LaunchShape{128, 4, 3};
-            d.shape[1] = d.n_links > 0 ? LaunchShape{64, 1, 2} : LaunchShape{128, 2, 1};
+            // 2 stages with them); odd step 256 x 1 (FP16: staged index tiles)
+            // without links, 64 x 1 (FP16: 128 x 1 register-bounded) with them
+            if (f16) d.shape[0] = links ? LaunchShape{128, 2, 1} : LaunchShape{128, 4, 3};
+            if (links) d.shape[1] = f16 ? LaunchShape{128, 1, 5} : LaunchShape{64, 1, 2};
+            else d.shape[1] = f16 ? LaunchShape{128, 2, 1} : LaunchShape{256, 1, 2};
         }
     }
     if (d.order == SLBM_ORDER_HYBRID) d.shape[1] = LaunchShape{128, 1, 2};   // its one odd shape

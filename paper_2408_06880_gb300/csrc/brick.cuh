@@ -131,11 +131,11 @@ __global__ void __launch_bounds__(256) aa_odd_brick_kernel(typename Store<ST>::T
         e[i] = r < 0 ? inv(i) * S + k - shift : __ldcs(fb + off + r);
     });
     float g[Q];
-    g[0] = St::raw(pdf[k]);
+    g[0] = St::raw(__ldg(pdf + k));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         R[i] = (HAS_BC && e[i] < 0) ? i * S + k : e[i];
-        g[i] = St::raw(pdf[R[i]]);
+        g[i] = St::raw(__ldg(pdf + R[i]));
     }
     const Vel u = collide<Q, St::scaled>(g, p);
     pdf[k] = St::pack(g[0]);

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
     const int32_t nxy = nx * ny;
     I R[Q];
     float g[Q];
-    g[0] = St::raw(pdf[v]);
+    g[0] = St::raw(__ldg(pdf + v));
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (m >> i & 1u) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128) dense_odd_kernel(typename Store<ST>::T *_
             zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
             R[i] = (I)inv(i) * s + (I)(xn + nx * (yn + ny * zn));
         }
-        g[i] = St::raw(pdf[R[i]]);
+        g[i] = St::raw(__ldg(pdf + R[i]));
     }
     collide<Q, St::scaled>(g, p);
     pdf[v] = St::pack(g[0]);
