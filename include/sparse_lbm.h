@@ -330,9 +330,9 @@ slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher);
  * and 5 (MRT also 2) with 1 or 2 cells per thread and odd variants 0, 2, 3
  * (no links) and 5; the rest SLBM_EUNSUPPORTED.  The hybrid cell order runs
  * one odd shape: 128 x 1, variant 2 (the full bricks by their own kernel).
- * Defaults: even variant 2, 64 x 4 (FP16 D3Q27: variant 3, tile 128, 4
- * stages, or with inlet/outlet links variant 1, tile 128, 2 stages; FP32
- * MRT: variant 2, 64 x 2; FP16 MRT and BF16: variant 0, 64 x 2;
+ * Defaults: even variant 2, 64 x 4 (FP16 D3Q27 with inlet/outlet links:
+ * variant 1, tile 128, 2 stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and
+ * BF16: variant 0, 64 x 2;
  * central-moment and cumulant: variant 5, 128 x 1); odd variant 2, 128 x 1
  * (FP16 D3Q19: 256 x 1; D3Q27 without links: FP32 variant 2, 256 x 1, FP16
  * variant 1, tile 128, 2 stages; D3Q27 with links: FP32 variant 2, 64 x 1,

@@ -43,8 +43,32 @@ __device__ __forceinline__ void st_vec(T *p, const Vec<T, N> &x) {
     *reinterpret_cast<Vec<T, N> *>(p) = x;
 }
 
+// ld_vec through the read-only data path (2, 4, 8 or 16 bytes).
+template <class T, int N>
+__device__ __forceinline__ Vec<T, N> ldg_vec(const T *p) {
+    constexpr int B = (int)sizeof(Vec<T, N>);
+    static_assert(B == 2 || B == 4 || B == 8 || B == 16, "vector of 2, 4, 8 or 16 bytes");
+    Vec<T, N> r;
+    if constexpr (B == 2) {
+        const unsigned short x = __ldg(reinterpret_cast<const unsigned short *>(p));
+        memcpy(&r, &x, 2);
+    } else if constexpr (B == 4) {
+        const unsigned int x = __ldg(reinterpret_cast<const unsigned int *>(p));
+        memcpy(&r, &x, 4);
+    } else if constexpr (B == 8) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
+        memcpy(&r, &x, 8);
+    } else {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+        memcpy(&r, &x, 16);
+    }
+    return r;
+}
+
 // A row segment of CPT consecutive cells: stored values <-> floats in stored
-// units.  FP16 pairs convert with the packed half2 forms (same rounding as
+// units.  load_ro (global memory only) takes the read-only data path: in the
+// even step a cell reads its own slots and writes its own slots (rows i and
+// inverse(i) of its column), which no other cell touches.  FP16 pairs convert with the packed half2 forms (same rounding as
 // element-wise conversion, half the instructions on the store side).
 template <int ST, int CPT>
 struct RowIO {
@@ -52,6 +76,11 @@ struct RowIO {
     using T = typename St::T;
     static __device__ __forceinline__ void load(const T *p, float (&f)[CPT]) {
         const Vec<T, CPT> x = ld_vec<T, CPT>(p);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) f[c] = St::raw(x.v[c]);
+    }
+    static __device__ __forceinline__ void load_ro(const T *p, float (&f)[CPT]) {   // global memory only
+        const Vec<T, CPT> x = ldg_vec<T, CPT>(p);
 #pragma unroll
         for (int c = 0; c < CPT; ++c) f[c] = St::raw(x.v[c]);
     }
@@ -71,6 +100,19 @@ struct RowIO<ST_F16, CPT> {
             f[0] = __half2float(*p);
         } else {
             const Vec<__half2, CPT / 2> x = ld_vec<__half2, CPT / 2>(reinterpret_cast<const __half2 *>(p));
+#pragma unroll
+            for (int c = 0; c < CPT / 2; ++c) {
+                const float2 v = __half22float2(x.v[c]);
+                f[2 * c] = v.x;
+                f[2 * c + 1] = v.y;
+            }
+        }
+    }
+    static __device__ __forceinline__ void load_ro(const __half *p, float (&f)[CPT]) {   // global memory only
+        if constexpr (CPT == 1) {
+            f[0] = __half2float(__ldg(p));
+        } else {
+            const Vec<__half2, CPT / 2> x = ldg_vec<__half2, CPT / 2>(reinterpret_cast<const __half2 *>(p));
 #pragma unroll
             for (int c = 0; c < CPT / 2; ++c) {
                 const float2 v = __half22float2(x.v[c]);
@@ -210,7 +252,7 @@ __device__ __forceinline__ void aa_even_cells(typename Store<ST>::T *__restrict_
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float f[CPT];
-        RowIO<ST, CPT>::load(pdf + i * S + k0, f);
+        RowIO<ST, CPT>::load_ro(pdf + i * S + k0, f);
 #pragma unroll
         for (int c = 0; c < CPT; ++c) g[c][i] = f[c];
     }

@@ -118,10 +118,10 @@ static void default_shapes(Domain &d) {
         if (d.q == 19) {
             if (f16) d.shape[1] = LaunchShape{256, 1, 2};
         } else {
-            // D3Q27: FP16 even step from bulk-staged tiles (paired without links,
-            // 2 stages with them); odd step 256 x 1 (FP16: staged index tiles)
-            // without links, 64 x 1 (FP16: 128 x 1 register-bounded) with them
-            if (f16) d.shape[0] = links ? LaunchShape{128, 2, 1} : LaunchShape{128, 4, 3};
+            // D3Q27: the FP16 even step with links from bulk-staged tiles (2
+            // stages); odd step 256 x 1 (FP16: staged index tiles) without links,
+            // 64 x 1 (FP16: 128 x 1 register-bounded) with them
+            if (f16 && links) d.shape[0] = LaunchShape{128, 2, 1};
             if (links) d.shape[1] = f16 ? LaunchShape{128, 1, 5} : LaunchShape{64, 1, 2};
             else d.shape[1] = f16 ? LaunchShape{128, 2, 1} : LaunchShape{256, 1, 2};
         }

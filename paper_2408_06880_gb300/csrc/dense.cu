@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(128) dense_even_kernel(typename Store<ST>::T *
     for (int i = 0; i < Q; ++i) {
         float f[2];
         if (two) {
-            RowIO<ST, 2>::load(pdf + (I)i * s + v0, f);
+            RowIO<ST, 2>::load_ro(pdf + (I)i * s + v0, f);
         } else {
             f[0] = St::raw(pdf[(I)i * s + v0]);
             f[1] = 0.f;
