@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
         float g[CPT][Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const Vec<T, CPT> x = ld_vec<T, CPT>(pdf + i * S + k0);
+            const Vec<T, CPT> x = ldg_vec<T, CPT>(pdf + i * S + k0);   // own slots only: read-only path
 #pragma unroll
             for (int c = 0; c < CPT; ++c) g[c][i] = St::raw(x.v[c]);
         }
