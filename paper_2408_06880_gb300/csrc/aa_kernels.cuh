@@ -137,30 +137,6 @@ struct RowIO<ST_F16, CPT> {
     }
 };
 
-// Index entries are read once per odd step: stream them past L2 (evict-first).
-template <int N>
-__device__ __forceinline__ Vec<int32_t, N> ld_index(const int32_t *p) {
-    if constexpr (N == 1) {
-        Vec<int32_t, 1> r;
-        r.v[0] = __ldcs(p);
-        return r;
-    } else if constexpr (N == 2) {
-        const int2 a = __ldcs(reinterpret_cast<const int2 *>(p));
-        Vec<int32_t, 2> r;
-        r.v[0] = a.x;
-        r.v[1] = a.y;
-        return r;
-    } else {
-        const int4 a = __ldcs(reinterpret_cast<const int4 *>(p));
-        Vec<int32_t, 4> r;
-        r.v[0] = a.x;
-        r.v[1] = a.y;
-        r.v[2] = a.z;
-        r.v[3] = a.w;
-        return r;
-    }
-}
-
 // Collision of the CPT cells a thread holds (g[c][i]: cell c, direction i).
 // PACK (CPT even): cells c and c + 1 share one pass of the
 // collision in the two lanes of the paired FP32 instructions -- the same
@@ -382,7 +358,7 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
                 const int32_t k = kb + c * blockDim.x;
-                cc[c][i] = valid[c] ? __ldcs(code + (i - 1) * S + k) : CODE_WALL;
+                cc[c][i] = valid[c] ? __ldg(code + (i - 1) * S + k) : CODE_WALL;
             }
         }
 #pragma unroll
@@ -404,7 +380,7 @@ __device__ __forceinline__ void aa_odd_body(typename Store<ST>::T *__restrict__ 
             for (int c = 0; c < CPT; ++c) {
                 const int32_t k = kb + c * blockDim.x;
                 if (RELOAD) e[c][i] = P[(i - 1) * S + k];
-                else e[c][i] = valid[c] ? __ldcs(P + (i - 1) * S + k) : 0;
+                else e[c][i] = valid[c] ? __ldg(P + (i - 1) * S + k) : 0;
             }
         }
     }

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) aa_odd_brick_kernel(typename Store<ST>::T
         constexpr int off = face_offset(i);
         constexpr int shift = cx(i) + 8 * cy(i) + 64 * cz(i);
         const int r = face_rank<Q>(i, lx, ly, lz);
-        e[i] = r < 0 ? inv(i) * S + k - shift : __ldcs(fb + off + r);
+        e[i] = r < 0 ? inv(i) * S + k - shift : __ldg(fb + off + r);
     });
     float g[Q];
     g[0] = St::raw(__ldg(pdf + k));

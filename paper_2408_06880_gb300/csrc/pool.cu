@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128, 4) pool_step_kernel(const PoolHeader *__r
                 int32_t e[Q];
                 e[0] = 0;
 #pragma unroll
-                for (int i = 1; i < Q; ++i) e[i] = __ldcs(R + (i - 1) * S + k);
+                for (int i = 1; i < Q; ++i) e[i] = __ldg(R + (i - 1) * S + k);
                 // one link-aware path: members without inlet/outlet links
                 // never take its branch
                 if constexpr (UNI) odd_cell<Q, ST, true>(pdf, e, k, S, sE.maps, up);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(POOL_THREADS) pool_tile_kernel(const PoolEntry
         int32_t e[Q];
         e[0] = 0;
 #pragma unroll
-        for (int i = 1; i < Q; ++i) e[i] = __ldcs(D.R + (i - 1) * S + k);
+        for (int i = 1; i < Q; ++i) e[i] = __ldg(D.R + (i - 1) * S + k);
         asm volatile("" ::: "memory");       // the loads above stay ahead of the test
         if (halt) return;
         // members without links never take the link branch of the BC path
