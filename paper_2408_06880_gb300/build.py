@@ -20,7 +20,9 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libsparse_lbm.so")
 
-SOURCES = ["api.cu", "lists.cu", "aa_q19.cu", "aa_q27.cu", "macro.cu", "dense.cu", "pool.cu", "pull.cu", "convert.cu"]
+SOURCES = ["api.cu", "lists.cu", "aa_dispatch.cu", "aa_q19_f32.cu", "aa_q19_f16.cu", "aa_q19_bf16.cu",
+           "aa_q27_f32.cu", "aa_q27_f16.cu", "aa_q27_bf16.cu", "macro.cu", "dense.cu", "pool.cu", "pull.cu",
+           "convert.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: every multiply and add is rounded separately, in program order,
 # so all kernel instantiations (launch shapes, batched or not) produce the same

@@ -240,8 +240,10 @@ static cudaError_t launch_even_packed(const Domain &d, const LaunchShape &sh, cu
     }
 }
 
+// One AA step of a domain with stencil Q and storage ST (instantiated per
+// stencil and storage in aa_q<Q>_<storage>.cu).
 template <int Q, int ST>
-static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
+cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t st) {
     using T = typename Store<ST>::T;
     T *pdf = reinterpret_cast<T *>(d.pdf.p);
     const int32_t S = (int32_t)d.S, nf = (int32_t)d.n_fluid;
@@ -347,26 +349,6 @@ static cudaError_t launch_aa_storage(const Domain &d, int parity, cudaStream_t s
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-// Fix-ups for the pool's even step (per member with links).
-template <int Q>
-cudaError_t launch_bc_fixup_q(const Domain &d, int post, cudaStream_t st) {
-    switch (d.storage) {
-        case SLBM_FP32: return post ? launch_bc_post<Q, ST_F32>(d, st) : launch_bc_pre<Q, ST_F32>(d, st);
-        case SLBM_FP16: return post ? launch_bc_post<Q, ST_F16>(d, st) : launch_bc_pre<Q, ST_F16>(d, st);
-        default: return post ? launch_bc_post<Q, ST_BF16>(d, st) : launch_bc_pre<Q, ST_BF16>(d, st);
-    }
-}
-
-template <int Q>
-cudaError_t launch_aa_step_q(const Domain &d, int parity, cudaStream_t st) {
-    switch (d.storage) {
-        case SLBM_FP32: return launch_aa_storage<Q, ST_F32>(d, parity, st);
-        case SLBM_FP16: return launch_aa_storage<Q, ST_F16>(d, parity, st);
-        case SLBM_BF16: return launch_aa_storage<Q, ST_BF16>(d, parity, st);
-    }
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace slbm
