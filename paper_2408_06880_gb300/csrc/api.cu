@@ -116,14 +116,14 @@ static void default_shapes(Domain &d) {
         const bool f16 = d.storage == SLBM_FP16, links = d.n_links > 0;
         d.shape[0] = LaunchShape{64, 4, 2};
         if (d.q == 19) {
-            if (f16) d.shape[1] = LaunchShape{256, 1, 2};
+            d.shape[1] = f16 ? LaunchShape{256, 1, 2} : LaunchShape{128, 2, 2};
         } else {
             // D3Q27: the FP16 even step with links from bulk-staged tiles (2
-            // stages); odd step 256 x 1 (FP16: staged index tiles) without links,
-            // 64 x 1 (FP16: 128 x 1 register-bounded) with them
+            // stages); odd step 256 x 1 (FP16: 256 x 2) without links, 64 x 1
+            // (FP16: 128 x 1 register-bounded) with them
             if (f16 && links) d.shape[0] = LaunchShape{128, 2, 1};
             if (links) d.shape[1] = f16 ? LaunchShape{128, 1, 5} : LaunchShape{64, 1, 2};
-            else d.shape[1] = f16 ? LaunchShape{128, 2, 1} : LaunchShape{256, 1, 2};
+            else d.shape[1] = f16 ? LaunchShape{256, 2, 2} : LaunchShape{256, 1, 2};
         }
     }
     if (d.order == SLBM_ORDER_HYBRID) d.shape[1] = LaunchShape{128, 1, 2};   // its one odd shape

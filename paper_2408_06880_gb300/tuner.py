@@ -24,7 +24,7 @@ EVEN_SHAPES = [(64, 1, 0), (64, 2, 0), (128, 2, 0), (64, 4, 0), (128, 2, 1), (12
                (64, 2, 2), (128, 2, 2), (64, 4, 2), (128, 2, 3), (128, 4, 3), (64, 2, 3), (128, 1, 0),
                (128, 1, 5)]
 ODD_SHAPES = [(128, 1, 2), (64, 1, 2), (256, 1, 2), (128, 1, 3), (256, 1, 3), (128, 1, 4), (64, 1, 4), (128, 1, 0),
-              (128, 2, 1), (256, 1, 5), (128, 1, 5)]
+              (128, 2, 1), (256, 1, 5), (128, 1, 5), (64, 2, 2), (128, 2, 2), (256, 2, 2)]
 POOL_SHAPES = [(64, 0), (64, 8), (128, 4), (96, 4)]
 
 _lock = threading.Lock()
