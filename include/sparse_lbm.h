@@ -334,7 +334,7 @@ slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher);
  * variant 1, tile 128, 2 stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and
  * BF16: variant 0, 64 x 2;
  * central-moment and cumulant: variant 5, 128 x 1); odd variant 2 (D3Q19:
- * FP32 128 x 2, FP16 256 x 1; D3Q27 without links: FP32 256 x 1, FP16
+ * FP32 128 x 2, or 128 x 1 with links, FP16 256 x 1; D3Q27 without links: FP32 256 x 1, FP16
  * 256 x 2; D3Q27 with links: FP32 64 x 1, FP16 variant 5, 128 x 1; BF16 and
  * the pull and dense layouts 128 x 1; MRT, central-moment and cumulant:
  * variant 5, 128 x 1).  Results are bit-for-bit the same for every shape. */

@@ -116,7 +116,9 @@ static void default_shapes(Domain &d) {
         const bool f16 = d.storage == SLBM_FP16, links = d.n_links > 0;
         d.shape[0] = LaunchShape{64, 4, 2};
         if (d.q == 19) {
-            d.shape[1] = f16 ? LaunchShape{256, 1, 2} : LaunchShape{128, 2, 2};
+            // FP32 without links: two cells a thread (the link maps would hold
+            // both cells' entries through the collision)
+            d.shape[1] = f16 ? LaunchShape{256, 1, 2} : links ? LaunchShape{128, 1, 2} : LaunchShape{128, 2, 2};
         } else {
             // D3Q27: the FP16 even step with links from bulk-staged tiles (2
             // stages); odd step 256 x 1 (FP16: 256 x 2) without links, 64 x 1
