@@ -332,12 +332,13 @@ slbm_status sparse_lbm_set_cm_rates(slbm_t *h, double bulk, double higher);
  * one odd shape: 128 x 1, variant 2 (the full bricks by their own kernel).
  * Defaults: even variant 2, 64 x 4 (FP16 D3Q27 with inlet/outlet links:
  * variant 1, tile 128, 2 stages; FP32 MRT: variant 2, 64 x 2; FP16 MRT and
- * BF16: variant 0, 64 x 2;
- * central-moment and cumulant: variant 5, 128 x 1); odd variant 2 (D3Q19:
- * FP32 128 x 2, or 128 x 1 with links, FP16 256 x 1; D3Q27 without links: FP32 256 x 1, FP16
- * 256 x 2; D3Q27 with links: FP32 64 x 1, FP16 variant 5, 128 x 1; BF16 and
- * the pull and dense layouts 128 x 1; MRT, central-moment and cumulant:
- * variant 5, 128 x 1).  Results are bit-for-bit the same for every shape. */
+ * BF16: variant 0, 64 x 2; central-moment and cumulant: variant 0, 64 x 1,
+ * 16-bit storage 64 x 2); odd variant 2 (D3Q19: FP32 128 x 2, or 128 x 1
+ * with links, FP16 256 x 1; D3Q27 without links: FP32 256 x 1, FP16
+ * 256 x 2; D3Q27 with links: FP32 64 x 1, FP16 variant 5, 128 x 1; BF16,
+ * the pull and dense layouts 128 x 1; MRT: variant 5, 128 x 1;
+ * central-moment and cumulant: 256 x 1).  Results are bit-for-bit the same
+ * for every shape. */
 slbm_status sparse_lbm_set_launch(slbm_t *h, int32_t parity, int32_t threads, int32_t cells, int32_t variant);
 
 /* Kernel check mode: 1 = odd-step gathers bounds-check every slot and latch

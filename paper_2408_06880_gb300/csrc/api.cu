@@ -98,17 +98,17 @@ CollideParams Domain::collide_params() const {
 // Default launch shapes of a domain's operator, storage and links (called
 // once its lists exist).  Even step: cells collided in pairs (measured faster
 // except for FP16 MRT and untimed BF16); FP16 D3Q27 from bulk-staged tiles;
-// the central-moment and cumulant collisions 128 x 1, register-bounded.  Odd
-// step: 128 x 1 with the L2 index prefetch, register-bounded for the
-// moment-space operators; D3Q27 as below.  All measured fastest on the 256^3
+// the central-moment and cumulant collisions 64 x 1 (16-bit: 64 x 2).  Odd
+// step: 128 x 1 with the L2 index prefetch (MRT: register-bounded;
+// central-moment and cumulant: 256 x 1); D3Q19 and D3Q27 as below.  All measured fastest on the 256^3
 // porosity-0.5 domain and, with links, on the particle bed.
 static void default_shapes(Domain &d) {
     d.shape[0] = LaunchShape{64, 2, 0};
     d.shape[1] = LaunchShape{128, 1, 2};
     if (d.layout != SLBM_LAYOUT_SPARSE) return;
-    if (d.op == SLBM_CM || d.op == SLBM_CUMULANT) {              // register-bounded, both steps
-        d.shape[0] = LaunchShape{128, 1, 5};
-        d.shape[1] = LaunchShape{128, 1, 5};
+    if (d.op == SLBM_CM || d.op == SLBM_CUMULANT) {
+        d.shape[0] = d.storage == SLBM_FP32 ? LaunchShape{64, 1, 0} : LaunchShape{64, 2, 0};
+        d.shape[1] = LaunchShape{256, 1, 2};
     } else if (d.op == SLBM_MRT) {                                // paired even step in FP32
         if (d.storage == SLBM_FP32) d.shape[0] = LaunchShape{64, 2, 2};
         d.shape[1] = LaunchShape{128, 1, 5};
