@@ -221,6 +221,49 @@ def test_even_links_with_ragged_last_tiles(residue, storage):
         assert np.array_equal(got, want), shape
 
 
+def _all_boundary_slab(q_seed=3):
+    """A 3-voxel-thick slab between a velocity inlet (x = 0) and a pressure
+    outlet (x = 2), periodic in y and z: every fluid cell has links, so a
+    block of the even kernels holds more links than threads."""
+    nz, ny, nx = 40, 33, 3
+    f = np.zeros((nz, ny, nx), np.uint8)
+    f[:, :, 0] = G.INLET
+    f[:, :, 2] = G.OUTLET
+    rng = np.random.default_rng(q_seed)
+    f[:, :, 1][rng.random((nz, ny)) < 0.2] = G.WALL
+    n_in = int(np.count_nonzero(f == G.INLET))
+    return G.Geometry(f, 0b110, rng.uniform(0.0, 0.03, (n_in, 3)), 1.002, {})
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("storage", [P.FP32, P.FP16])
+def test_even_links_more_links_than_threads(q, storage):
+    # every cell a boundary cell: the even kernels' link pass walks several
+    # links per thread; all even shapes give the bits of 128 x 1, and FP32
+    # stays within the FP64 oracle's tolerance
+    g = _all_boundary_slab()
+    kw = dict(q=q, op=P.TRT, force=(0.0, 0.0, 0.0), storage=storage, scale_exp=18)
+    with gpu_domain(g, **kw) as ref:
+        assert ref.info["n_bc_links"] > 4 * ref.n_fluid
+        ref.set_launch(0, 128, 1)
+        ref.step(6)
+        want, _ = ref.get_state()
+        rho, u = ref.macroscopic(P.ORDER_CELLS)
+    for shape in ((32, 1, 0), (64, 2, 0), (32, 4, 0), (64, 2, 2), (64, 4, 2), (64, 2, 1), (128, 2, 1), (64, 2, 3)):
+        with gpu_domain(g, **kw) as d:
+            d.set_launch(0, *shape)
+            d.step(6)
+            got, _ = d.get_state()
+            assert d.device_error() == 0
+        assert np.array_equal(got, want), shape
+    if storage == P.FP32:
+        p = O.Problem.from_geometry(g, q=q, op=O.TRT, omega_plus=1.25, magic=3 / 16, force=(0.0, 0.0, 0.0))
+        L = O.pull_list(p)
+        rho_o, u_o = O.sparse_macroscopic(p, L, O.sparse_run(p, L, O.sparse_rest(p, L), 6))
+        assert rel_l2(u.T, u_o) <= 1e-5
+        assert np.max(np.abs(rho - rho_o)) <= 1e-6
+
+
 @pytest.mark.parametrize("stages", [2, 3, 4])
 @pytest.mark.parametrize("case", ["sweep96_lex", "sweep96_brick", "dense96", "bed_links", "bf16"])
 def test_window_staged_odd_step_over_many_tiles(case, stages):
