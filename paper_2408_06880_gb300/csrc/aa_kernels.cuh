@@ -264,6 +264,18 @@ __device__ __forceinline__ void aa_even_body(typename Store<ST>::T *__restrict__
         const int32_t ke = kb + span < nf ? kb + span : nf;
         int32_t b0, b1;
         even_link_range(lk, kb, ke, b0, b1);
+        // this thread's first link of the block's range: its cell, direction
+        // and map are loaded while the populations load, so that after the
+        // barrier only the slot's re-read remains
+        const int32_t lb = b0 + threadIdx.x;
+        const bool first = lb < b1;
+        int32_t lc = 0, ld = 0;
+        LinkMap lm{};
+        if (first) {
+            lc = lk.link_cell[lb] - kb;
+            ld = lk.link_dir[lb];
+            lm = lk.maps[lb];
+        }
         Vel u[CPT] = {};
         if (k0 < nf) aa_even_cells<Q, ST, CPT, OP, PACK>(pdf, S, nf, p, k0, u);
         if (b0 == b1) return;                         // uniform across the block
@@ -275,7 +287,13 @@ __device__ __forceinline__ void aa_even_body(typename Store<ST>::T *__restrict__
             even_us[2 * span + l] = u[c].z;
         }
         __syncthreads();
-        even_links_apply<ST>(pdf, S, kb, b0, b1, even_us, span, lk, p.scale);
+        if (first) {
+            using St = Store<ST>;
+            typename St::T *slot = pdf + ld * S + (kb + lc);
+            *slot = St::pack(apply_link(lm, St::raw(*slot), even_us[lc], even_us[span + lc], even_us[2 * span + lc],
+                                        p.scale));
+        }
+        even_links_apply<ST>(pdf, S, kb, lb + blockDim.x - threadIdx.x, b1, even_us, span, lk, p.scale);
     } else {
         if (k0 >= nf) return;
         Vel u[CPT];
